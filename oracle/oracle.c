@@ -1,0 +1,347 @@
+/*
+ * oracle.c -- plain, slow, obviously-correct CPU oracle for successive-
+ * cancellation (SC) decoding of polar codes in syndrome form, after
+ * Jouguet & Kunz-Jacques, "High performance error correction for quantum key
+ * distribution using polar codes" (arXiv 1204.5882).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path links, loads or
+ * calls this file: only the tests, the smoke check and the benchmark's CPU
+ * baseline leg do.  It shares no code, header, table or helper with the CUDA
+ * library under paper_1204_5882_gb300/csrc.
+ *
+ * Conventions (the paper gives no formula for the transform, Sec. 3):
+ *   - one bit per uint8_t (0/1), index i = position in natural order;
+ *   - x = u * F^{(x)n},  F = [[1,0],[1,1]], no bit-reversal permutation;
+ *     splitting u = (a, b) in halves gives x = (aG' ^ bG', bG');
+ *   - LLR L = ln P(y|x=0)/P(y|x=1); decision on an information leaf:
+ *     u = 1 iff L < 0 (so L = +0.0 and L = -0.0 both decide 0).
+ *
+ * Parity pins (tests/test_oracle_*.py):
+ *   encode          -- involution, N=2 closed form, explicit Kronecker product;
+ *   f / g           -- N=2 closed form, literal 2*atanh(tanh*tanh);
+ *   SC exact f      -- brute-force bit-channel LLR (sum over all future bits);
+ *   SC min-sum      -- brute-force max-log bit-channel LLR, bit-exact on
+ *                      small-integer LLRs, ties included;
+ *   construction    -- BEC brute force of bit-channel erasure probabilities,
+ *                      conservation, GA vs numerically integrated phi;
+ *   capacity        -- closed forms and independent quadrature.
+ */
+#define _GNU_SOURCE
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_API __attribute__((visibility("default")))
+
+/* ------------------------------------------------------------------------ */
+/* Arikan transform (Sec. 3: channels combined recursively).                */
+/* x = u * F^{(x)n}: for every level the first half of each block of size   */
+/* 2h is XORed with its second half.  Applied in place.                     */
+/* ------------------------------------------------------------------------ */
+OR_API void or_encode(uint8_t *v, int n)
+{
+    size_t N = (size_t)1 << n;
+    for (size_t h = 1; h < N; h <<= 1)
+        for (size_t base = 0; base < N; base += 2 * h)
+            for (size_t j = 0; j < h; j++)
+                v[base + j] ^= v[base + h + j];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Channel LLRs (Sec. 1 and Sec. 2.2: BSC for DV-QKD, BI-AWGN for CV-QKD).  */
+/* BSC: L = (1-2y) * c with c = ln((1-p)/p) computed in double and rounded  */
+/* once to float.  BIAWGN: L = y * s with s = 2/sigma^2 in double, the      */
+/* product rounded to double and then once to float.  The double versions   */
+/* keep the double values.                                                  */
+/* ------------------------------------------------------------------------ */
+OR_API void or_llr_bsc_f32(const uint8_t *y, size_t n, double p, float *L)
+{
+    double c = log((1.0 - p) / p);
+    float cf = (float)c;
+    for (size_t i = 0; i < n; i++) L[i] = y[i] ? -cf : cf;
+}
+
+OR_API void or_llr_bsc_f64(const uint8_t *y, size_t n, double p, double *L)
+{
+    double c = log((1.0 - p) / p);
+    for (size_t i = 0; i < n; i++) L[i] = y[i] ? -c : c;
+}
+
+OR_API void or_llr_biawgn_f32(const double *y, size_t n, double sigma2, float *L)
+{
+    double s = 2.0 / sigma2;
+    for (size_t i = 0; i < n; i++) L[i] = (float)(y[i] * s);
+}
+
+OR_API void or_llr_biawgn_f64(const double *y, size_t n, double sigma2, double *L)
+{
+    double s = 2.0 / sigma2;
+    for (size_t i = 0; i < n; i++) L[i] = y[i] * s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Check-node update f (Sec. 4: LLR update through phi).                    */
+/* The paper names phi(x) = log(tanh(x/2)); its sign is garbled (that value */
+/* is negative for x > 0).  Read as Gallager's phi(x) = -ln tanh(x/2),      */
+/* which is its own inverse on (0, inf), so                                 */
+/*   f(a, b) = sgn(a) sgn(b) phi(phi(|a|) + phi(|b|))                       */
+/*           = 2 atanh(tanh(a/2) tanh(b/2)).                                */
+/* phi(x) = ln(1 + 2/(e^x - 1)) = log1p(2/expm1(x)) is accurate for both    */
+/* small and large x.  Min-sum replaces phi(phi(A)+phi(B)) by min(A, B).    */
+/* The sign of f is taken as - iff exactly one of a, b is negative          */
+/* (signbit); a zero magnitude gives a zero f, whose sign no decision reads.*/
+/* ------------------------------------------------------------------------ */
+static double phi64(double x) { return log1p(2.0 / expm1(x)); }
+static float phi32(float x) { return log1pf(2.0f / expm1f(x)); }
+
+OR_API double or_f_exact_f64(double a, double b)
+{
+    double A = fabs(a), B = fabs(b);
+    double m = phi64(phi64(A) + phi64(B));
+    return (signbit(a) != signbit(b)) ? -m : m;
+}
+
+OR_API float or_f_exact_f32(float a, float b)
+{
+    float A = fabsf(a), B = fabsf(b);
+    float m = phi32(phi32(A) + phi32(B));
+    return (signbit(a) != signbit(b)) ? -m : m;
+}
+
+OR_API double or_f_minsum_f64(double a, double b)
+{
+    double m = fmin(fabs(a), fabs(b));
+    return (signbit(a) != signbit(b)) ? -m : m;
+}
+
+OR_API float or_f_minsum_f32(float a, float b)
+{
+    float m = fminf(fabsf(a), fabsf(b));
+    return (signbit(a) != signbit(b)) ? -m : m;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Recursive SC decoder (Sec. 1: deterministic, O(N log N); Sec. 4:         */
+/* recursive).  Syndrome form (Sec. 1): frozen positions take Alice's       */
+/* revealed values fval[i] instead of zeros.                                */
+/*                                                                          */
+/* node(k, L[0..2^k)):                                                      */
+/*   k == 0 : u = frozen ? fval : (L < 0);  beta = u                        */
+/*   else   : h = 2^(k-1)                                                   */
+/*            Lc[j] = f(L[j], L[j+h])                    -> left child      */
+/*            Lc[j] = beta_L[j] ? L[j+h]-L[j] : L[j+h]+L[j] -> right child  */
+/*            beta  = (beta_L ^ beta_R, beta_R)                             */
+/* The root beta is x_hat = u_hat * F^{(x)n}.                               */
+/* ------------------------------------------------------------------------ */
+#define OR_DEFINE_SC(T, SUF, FEXACT, FMINSUM)                                  \
+    static void sc_node_##SUF(int k, const T *L, const uint8_t *frz,           \
+                              const uint8_t *fval, uint8_t *u, uint8_t *beta,  \
+                              int fkind, T *scratch, T *leaf)                  \
+    {                                                                          \
+        if (k == 0) {                                                          \
+            uint8_t d = frz[0] ? fval[0] : (uint8_t)(L[0] < (T)0);             \
+            u[0] = d;                                                          \
+            beta[0] = d;                                                       \
+            if (leaf) leaf[0] = L[0];                                          \
+            return;                                                            \
+        }                                                                      \
+        size_t h = (size_t)1 << (k - 1);                                       \
+        T *Lc = scratch;                                                       \
+        for (size_t j = 0; j < h; j++)                                         \
+            Lc[j] = fkind ? FEXACT(L[j], L[j + h]) : FMINSUM(L[j], L[j + h]);  \
+        sc_node_##SUF(k - 1, Lc, frz, fval, u, beta, fkind, scratch + h,       \
+                      leaf);                                                   \
+        for (size_t j = 0; j < h; j++)                                         \
+            Lc[j] = beta[j] ? (L[j + h] - L[j]) : (L[j + h] + L[j]);           \
+        sc_node_##SUF(k - 1, Lc, frz + h, fval + h, u + h, beta + h, fkind,    \
+                      scratch + h, leaf ? leaf + h : NULL);                    \
+        for (size_t j = 0; j < h; j++) beta[j] ^= beta[j + h];                 \
+    }                                                                          \
+    OR_API int or_sc_decode_##SUF(int n, int fkind, const T *llr,             \
+                                  const uint8_t *frozen, const uint8_t *fval,  \
+                                  uint8_t *u_hat, uint8_t *x_hat, T *leaf)     \
+    {                                                                          \
+        size_t N = (size_t)1 << n;                                             \
+        T *scratch = (T *)malloc(sizeof(T) * (N > 1 ? N : 1));                 \
+        if (!scratch) return -1;                                               \
+        sc_node_##SUF(n, llr, frozen, fval, u_hat, x_hat, fkind, scratch,      \
+                      leaf);                                                   \
+        free(scratch);                                                         \
+        return 0;                                                              \
+    }
+
+OR_DEFINE_SC(double, f64, or_f_exact_f64, or_f_minsum_f64)
+OR_DEFINE_SC(float, f32, or_f_exact_f32, or_f_minsum_f32)
+
+/* ------------------------------------------------------------------------ */
+/* Frozen-set construction (Sec. 3: density evolution selects the frozen    */
+/* bits as the lowest-capacity bit-channels).  The paper uses the method of */
+/* Mori-Tanaka; this oracle implements the two standard substitutes:        */
+/*   BSC    -- Bhattacharyya parameters, Z- <= 2Z - Z^2 (upper bound),      */
+/*             Z+ = Z^2, Z0 = 2 sqrt(p(1-p));                               */
+/*   BIAWGN -- Gaussian approximation of density evolution, m0 = 2/sigma^2, */
+/*             m+ = 2m, m- = phiGA^-1(1 - (1 - phiGA(m))^2),                */
+/*             P_e = Q(sqrt(m/2)).                                           */
+/* Index convention: z'[2j] = minus(z[j]), z'[2j+1] = plus(z[j]), so the    */
+/* first polarisation step lands in the most significant index bit, which   */
+/* is the top split (u first half / second half) of the natural-order       */
+/* decoder above.  Everything is kept in the log domain (ln Z, ln phiGA) so */
+/* that nothing underflows at N = 2^24.                                     */
+/* ------------------------------------------------------------------------ */
+
+/* ln(2Z - Z^2) = lz + ln(2 - e^lz) = lz + log1p(-expm1(lz)). */
+static double bh_minus(double lz) { return lz + log1p(-expm1(lz)); }
+static double bh_plus(double lz) { return 2.0 * lz; }
+
+OR_API void or_bhatt_log_from(int n, double lz0, double *out)
+{
+    size_t N = (size_t)1 << n;
+    double *tmp = (double *)malloc(sizeof(double) * N);
+    out[0] = lz0;
+    for (int s = 0; s < n; s++) {
+        size_t len = (size_t)1 << s;
+        for (size_t j = 0; j < len; j++) {
+            tmp[2 * j] = bh_minus(out[j]);
+            tmp[2 * j + 1] = bh_plus(out[j]);
+        }
+        memcpy(out, tmp, sizeof(double) * 2 * len);
+    }
+    free(tmp);
+}
+
+OR_API void or_bhatt_log_bsc(int n, double p, double *out)
+{
+    double lz0 = log(2.0) + 0.5 * (log(p) + log1p(-p));
+    or_bhatt_log_from(n, lz0, out);
+}
+
+/* Chung-Richardson-Urbanke phi for the Gaussian approximation, in logs.   */
+/*   x < 10 : phiGA(x) = exp(-0.4527 x^0.86 + 0.0218)                       */
+/*   x >= 10: phiGA(x) = sqrt(pi/x) exp(-x/4) (1 - 10/(7x))                 */
+OR_API double or_ga_lnphi(double x)
+{
+    if (x < 10.0) return -0.4527 * pow(x, 0.86) + 0.0218;
+    return 0.5 * log(M_PI / x) - 0.25 * x + log1p(-10.0 / (7.0 * x));
+}
+
+/* Inverse of ln phiGA.  ln phiGA is decreasing on each piece but jumps up  */
+/* at x = 10 (left limit -3.2576, right value -3.2331), so targets inside   */
+/* the jump have one preimage on each piece.  Reading taken: the x < 10     */
+/* piece is used whenever its range contains t (closed-form inverse);       */
+/* otherwise the x >= 10 piece is inverted by bisection, doubling the       */
+/* bracket until it contains the root and halving until it cannot shrink.   */
+OR_API double or_ga_lnphi_inv(double t)
+{
+    double left10 = -0.4527 * pow(10.0, 0.86) + 0.0218;
+    if (t > left10) {
+        double v = (0.0218 - t) / 0.4527;
+        return v > 0.0 ? pow(v, 1.0 / 0.86) : 0.0;
+    }
+    double lo = 10.0, hi = 20.0;
+    while (or_ga_lnphi(hi) > t) { lo = hi; hi *= 2.0; }
+    for (;;) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (or_ga_lnphi(mid) > t) lo = mid; else hi = mid;
+    }
+    return hi;
+}
+
+/* m- : 1 - phi(m-) = (1 - phi(m))^2  <=>  phi(m-) = phi(m) (2 - phi(m)).  */
+static double ga_minus(double m)
+{
+    double lp = or_ga_lnphi(m);
+    double t = lp + log1p(-expm1(lp)); /* ln(phi (2 - phi)) */
+    return or_ga_lnphi_inv(t);
+}
+
+OR_API void or_ga_mean(int n, double sigma2, double *out)
+{
+    size_t N = (size_t)1 << n;
+    double *tmp = (double *)malloc(sizeof(double) * N);
+    out[0] = 2.0 / sigma2;
+    for (int s = 0; s < n; s++) {
+        size_t len = (size_t)1 << s;
+        for (size_t j = 0; j < len; j++) {
+            tmp[2 * j] = ga_minus(out[j]);
+            tmp[2 * j + 1] = 2.0 * out[j];
+        }
+        memcpy(out, tmp, sizeof(double) * 2 * len);
+    }
+    free(tmp);
+}
+
+/* ln Q(x) for x >= 0: erfc for moderate x, asymptotic series for large x.   */
+OR_API double or_ln_q(double x)
+{
+    if (x < 30.0) return log(0.5 * erfc(x / M_SQRT2));
+    double x2 = x * x;
+    double s = 1.0 - 1.0 / x2 + 3.0 / (x2 * x2) - 15.0 / (x2 * x2 * x2);
+    return -0.5 * x2 - log(x) - 0.5 * log(2.0 * M_PI) + log(s);
+}
+
+/* ln P_e of each bit-channel under the Gaussian approximation. */
+OR_API void or_ga_lnpe(int n, double sigma2, double *out)
+{
+    size_t N = (size_t)1 << n;
+    or_ga_mean(n, sigma2, out);
+    for (size_t i = 0; i < N; i++) out[i] = or_ln_q(sqrt(out[i] / 2.0));
+}
+
+/* Selection: freeze the N-K least reliable bit-channels.  `bad[i]` grows   */
+/* with unreliability (ln Z or ln P_e).  Order: bad descending, ties broken */
+/* by index ascending (the lower index is frozen first).                    */
+static const double *g_bad;
+static int cmp_unrel(const void *pa, const void *pb)
+{
+    uint32_t a = *(const uint32_t *)pa, b = *(const uint32_t *)pb;
+    if (g_bad[a] > g_bad[b]) return -1;
+    if (g_bad[a] < g_bad[b]) return 1;
+    return (a < b) ? -1 : (a > b);
+}
+
+OR_API void or_select_frozen(int n, const double *bad, uint64_t K, uint8_t *frozen)
+{
+    size_t N = (size_t)1 << n;
+    uint32_t *idx = (uint32_t *)malloc(sizeof(uint32_t) * N);
+    for (size_t i = 0; i < N; i++) idx[i] = (uint32_t)i;
+    g_bad = bad;
+    qsort(idx, N, sizeof(uint32_t), cmp_unrel);
+    for (size_t i = 0; i < N; i++) frozen[i] = 0;
+    for (size_t r = 0; r < N - K; r++) frozen[idx[r]] = 1;
+    free(idx);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Capacities for the efficiency beta = R / C (Sec. 2.1, Eq. 3).            */
+/* BSC: C = 1 - h2(p).  BIAWGN with x = 0 sent (+1):                        */
+/*   C = 1 - E[log2(1 + exp(-2Y/sigma^2))],  Y ~ N(1, sigma^2),             */
+/* by the composite Simpson rule over +-12 sigma.                           */
+/* ------------------------------------------------------------------------ */
+OR_API double or_capacity_bsc(double p)
+{
+    if (p <= 0.0 || p >= 1.0) return 1.0;
+    return 1.0 + p * log2(p) + (1.0 - p) * log2(1.0 - p);
+}
+
+static double log2_1p_exp(double z) /* log2(1 + e^z), no overflow */
+{
+    if (z > 0) return (z + log1p(exp(-z))) / M_LN2;
+    return log1p(exp(z)) / M_LN2;
+}
+
+OR_API double or_capacity_biawgn(double sigma2)
+{
+    double sigma = sqrt(sigma2);
+    const int M = 200000; /* even */
+    double a = 1.0 - 12.0 * sigma, b = 1.0 + 12.0 * sigma, h = (b - a) / M;
+    double acc = 0.0;
+    for (int i = 0; i <= M; i++) {
+        double y = a + i * h;
+        double pdf = exp(-0.5 * (y - 1.0) * (y - 1.0) / sigma2) / (sigma * sqrt(2.0 * M_PI));
+        double w = (i == 0 || i == M) ? 1.0 : ((i & 1) ? 4.0 : 2.0);
+        acc += w * pdf * log2_1p_exp(-2.0 * y / sigma2);
+    }
+    return 1.0 - acc * h / 3.0;
+}
