@@ -1,0 +1,192 @@
+/*
+ * polar.h -- C ABI of the GB300 successive-cancellation (SC) polar decoder.
+ *
+ * The method is the error-correction step of QKD with polar codes, after
+ * Jouguet & Kunz-Jacques (arXiv 1204.5882):
+ *   - syndrome form (Sec. 1): Alice sends no codeword; Bob holds channel
+ *     LLRs of Alice's string x and Alice reveals u_F = (x G_N)_F, the
+ *     values of the frozen positions of u = x G_N;
+ *   - frozen set = the least reliable bit-channels (Sec. 3);
+ *   - recursive SC decoding with the phi-based LLR update (Sec. 4).
+ *
+ * Conventions shared by every entry point:
+ *   - N = 2^log2n, 1 <= log2n <= 26.  Transform x = u F^{(x)n} with
+ *     F = [[1,0],[1,1]] in natural order (no bit reversal); it is its own
+ *     inverse over GF(2).
+ *   - Bit vectors are packed little-endian in uint32 words: bit i of a
+ *     frame is bit (i % 32) of word (i / 32).  A frame of N bits takes
+ *     max(1, N/32) words; frames of a batch are contiguous.
+ *   - LLR L = ln P(y|x=0)/P(y|x=1).  An information bit decides 1 iff
+ *     L < 0 (both +0.0 and -0.0 decide 0).
+ *   - Every pointer named *_dev is device memory owned by the caller.  The
+ *     library owns frozen-set objects, its per-stream scratch workspace and
+ *     its cached CUDA graphs.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Decode and map calls are asynchronous and stream-ordered;
+ *     the outputs are ready when the stream reaches that point.
+ *   - Errors: a negative polar_status; nothing is thrown across the ABI.
+ *     Argument errors are detected on the host before any launch.
+ *     POLAR_ECUDA reports a CUDA error (polar_last_error_string() has the
+ *     CUDA text).
+ *
+ * Thread safety: calls on different streams may run from different host
+ * threads; frozen-set objects are read-only after construction.
+ */
+#ifndef POLAR_GB300_H
+#define POLAR_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    POLAR_OK = 0,
+    POLAR_EINVAL = -1,     /* bad argument (size, pointer, enum, alignment) */
+    POLAR_ENOMEM = -2,     /* host or device allocation failed */
+    POLAR_ECUDA = -3,      /* a CUDA runtime call or kernel launch failed */
+    POLAR_ETIMEDOUT = -4,  /* a bounded device-side wait expired */
+    POLAR_EBUSY = -5,      /* admission refused (server) */
+    POLAR_ENOTFOUND = -6,  /* unknown ticket or option */
+    POLAR_PENDING = 1      /* request still running (server poll) */
+} polar_status;
+
+typedef enum { POLAR_BSC = 0, POLAR_BIAWGN = 1 } polar_channel;
+typedef enum { POLAR_F_MINSUM = 0, POLAR_F_EXACT = 1 } polar_fkind;
+typedef enum { POLAR_FP32 = 0, POLAR_FP16 = 1, POLAR_INT8 = 2 } polar_prec;
+
+typedef struct polar_frozen_set polar_frozen_set;
+
+/* ------------------------------------------------------------------ misc */
+
+/* Text for a polar_status value (static storage). */
+const char *polar_strerror(int status);
+
+/* CUDA error text of the last POLAR_ECUDA on this host thread ("" if none). */
+const char *polar_last_error_string(void);
+
+/* Process-wide tuning knobs, by name.  Returns POLAR_ENOTFOUND for an
+ * unknown key, POLAR_EINVAL for a value out of range.  Keys:
+ *   "subtree_log2"  t, log2 of the leaves one CTA decodes in shared memory
+ *                   (5..13; default 13); levels above t stream through HBM.
+ *   "shortcuts"     1 = rate-0 / rate-1 node shortcuts (default), 0 = none.
+ *   "graphs"        1 = replay batch launch sequences as CUDA graphs
+ *                   (default), 0 = launch every kernel eagerly.
+ *   "plain"         1 = the plain per-frame baseline: frames decoded one
+ *                   after another, no shortcuts, no graphs; 0 (default).
+ */
+int polar_config_set(const char *key, long value);
+int polar_config_get(const char *key, long *value);
+
+/* --------------------------------------------------------- construction */
+
+/* Frozen set of the code of length N = 2^log2n and K = floor(rate * N)
+ * information bits for channel `ch` with parameter `param` (crossover
+ * probability p of the BSC, noise variance sigma^2 of the BI-AWGN channel
+ * with +-1 inputs).  Sec. 3: the N-K least reliable bit-channels are frozen.
+ * Reliability: Bhattacharyya recursion Z- = 2Z - Z^2, Z+ = Z^2 from
+ * Z0 = 2 sqrt(p(1-p)) (BSC); Gaussian approximation of density evolution
+ * m0 = 2/sigma^2, m+ = 2m, m- = phi^-1(1 - (1 - phi(m))^2),
+ * P_e = Q(sqrt(m/2)) (BI-AWGN).  Equal reliabilities freeze the lower index
+ * first.  Runs on the host in double precision; the device copy is made on
+ * first use.  *out receives a library-owned object (free with
+ * polar_frozen_set_free).  EINVAL: log2n outside 1..26, p outside (0, 0.5),
+ * sigma^2 <= 0, rate outside [0, 1], out == NULL. */
+int polar_build_frozen_set(uint32_t log2n, polar_channel ch, double param,
+                           double rate, polar_frozen_set **out);
+
+/* Frozen set from a caller-given mask (bit i set = position i frozen);
+ * mask_host holds max(1, N/32) words and is copied. */
+int polar_frozen_set_from_mask(uint32_t log2n, const uint32_t *mask_host,
+                               polar_frozen_set **out);
+
+/* Read back N's log2, K, the mask (N/32 words, caller-owned, nullable) and
+ * the sum over information bits of Z_i (BSC, a union bound on the frame
+ * error rate) or P_e,i (BI-AWGN, an estimate) -- Sec. 3's FER bound.
+ * Every output pointer may be NULL. */
+int polar_frozen_set_query(const polar_frozen_set *fs, uint32_t *log2n,
+                           uint64_t *k, uint32_t *mask_host,
+                           double *sum_pe_info);
+
+void polar_frozen_set_free(polar_frozen_set *fs);
+
+/* --------------------------------------------------------- channel LLRs */
+
+/* Channel LLRs for n_total symbols (Sec. 1 and 2.2: BSC for DV-QKD, BI-AWGN
+ * for CV-QKD).
+ *   BSC    (y_is_bits = 1): y_dev = packed bits, L = y ? -c : c with
+ *          c = ln((1-p)/p) computed in double and rounded once to float;
+ *          n_total must be a multiple of 32.
+ *   BIAWGN (y_is_bits = 0): y_dev = double[n_total],
+ *          L = float(double(y * double(2/sigma^2))).
+ * llr_dev: float[n_total].  EINVAL: NULL pointers, bad channel/parameter,
+ * wrong y format for the channel. */
+int polar_llr_from_channel(polar_channel ch, double param, const void *y_dev,
+                           int y_is_bits, float *llr_dev, size_t n_total,
+                           void *stream);
+
+/* ------------------------------------------------------ Alice-side helpers */
+
+/* out = in F^{(x)n} for each of nframes frames of N = 2^log2n bits (packed).
+ * in_dev == out_dev is allowed.  Used by Alice to compute u = x G_N. */
+int polar_encode(uint32_t log2n, int nframes, const uint32_t *in_dev,
+                 uint32_t *out_dev, void *stream);
+
+/* Syndrome-form reveal (Sec. 1): fval = (x G_N) AND mask, per frame.  This is
+ * the frozen-value vector the decoders take. */
+int polar_reveal(const polar_frozen_set *fs, int nframes, const uint32_t *x_dev,
+                 uint32_t *fval_dev, void *stream);
+
+/* ------------------------------------------------------------- decoding */
+
+/* SC decoding of one frame (Sec. 4).
+ *   llr_dev          float[N] channel LLRs;
+ *   frozen_vals_dev  packed u with Alice's values at frozen positions (bits
+ *                    at information positions are ignored);
+ *   xhat_dev         packed output x_hat = u_hat G_N (Bob's estimate of x);
+ *                    also used as the partial-sum store while decoding;
+ *   uhat_dev         packed output u_hat, or NULL;
+ *   fkind            min-sum f (bit-exact against a float32 recursive SC)
+ *                    or exact f = 2 atanh(tanh(a/2) tanh(b/2));
+ *   prec             storage precision of intermediate LLRs (FP16: round to
+ *                    nearest even and saturate at +-65504; INT8: per-frame
+ *                    power-of-two scale, round, saturate at +-127); every
+ *                    f and g is computed in float32.
+ * Scratch: the library grows a per-stream workspace with cudaMalloc on the
+ * first call that needs more (so that call must not be inside a stream
+ * capture); about N * bytes(prec) per frame. */
+int polar_sc_decode(const polar_frozen_set *fs, const float *llr_dev,
+                    const uint32_t *frozen_vals_dev, uint32_t *xhat_dev,
+                    uint32_t *uhat_dev, polar_fkind fkind, polar_prec prec,
+                    void *stream);
+
+/* Batch of nframes frames sharing one frozen set, stored contiguously:
+ * llr [nframes][N] floats, frozen_vals / xhat / uhat [nframes][N/32] words.
+ * One launch sequence decodes all frames together (replayed as a CUDA graph
+ * when "graphs" is on). */
+int polar_sc_decode_many(const polar_frozen_set *fs, int nframes,
+                         const float *llr_dev, const uint32_t *frozen_vals_dev,
+                         uint32_t *xhat_dev, uint32_t *uhat_dev,
+                         polar_fkind fkind, polar_prec prec, void *stream);
+
+/* One frame of a heterogeneous batch. */
+typedef struct {
+    const polar_frozen_set *fs;
+    const float *llr;              /* device, float[N] */
+    const uint32_t *frozen_vals;   /* device, packed */
+    uint32_t *xhat;                /* device, packed */
+    uint32_t *uhat;                /* device, packed, or NULL */
+} polar_frame_desc;
+
+/* Frames of any lengths and frozen sets.  Consecutive frames with the same
+ * frozen set whose buffers are equally strided are decoded as one batch. */
+int polar_sc_decode_batch(int nframes, const polar_frame_desc *frames,
+                          polar_fkind fkind, polar_prec prec, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POLAR_GB300_H */

@@ -1,0 +1,448 @@
+// C ABI of the GB300 SC polar decoder (include/polar.h): argument checks,
+// per-stream scratch, the streamed schedule of the SC recursion and its
+// replay as CUDA graphs.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <list>
+#include <tuple>
+
+#include "polar_internal.h"
+
+using namespace polar;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct Config {
+  std::atomic<long> subtree_log2{13};
+  std::atomic<long> shortcuts{1};
+  std::atomic<long> graphs{1};
+  std::atomic<long> plain{0};
+};
+Config g_cfg;
+
+int cuda_fail(cudaError_t e) {
+  g_last_error = cudaGetErrorString(e);
+  return POLAR_ECUDA;
+}
+
+#define CK(expr)                                   \
+  do {                                             \
+    cudaError_t e_ = (expr);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_);   \
+  } while (0)
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// ---------------------------------------------------------------- workspace
+struct Workspace {
+  void *ptr = nullptr;
+  size_t bytes = 0;
+};
+std::mutex g_ws_mu;
+std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
+
+int get_workspace(int dev, cudaStream_t s, size_t bytes, void **out) {
+  std::lock_guard<std::mutex> g(g_ws_mu);
+  Workspace &w = g_ws[{dev, s}];
+  if (w.bytes < bytes) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) {
+      g_last_error = "scratch workspace must grow, but the stream is being captured";
+      return POLAR_EINVAL;
+    }
+    if (w.ptr) {
+      CK(cudaStreamSynchronize(s));
+      cudaFree(w.ptr);
+      w.ptr = nullptr;
+      w.bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&w.ptr, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      w.ptr = nullptr;
+      g_last_error = cudaGetErrorString(e);
+      return POLAR_ENOMEM;
+    }
+    w.bytes = bytes;
+  }
+  *out = w.ptr;
+  return POLAR_OK;
+}
+
+// ---------------------------------------------------------------- graphs
+using GraphKey = std::tuple<uint64_t, int, const void *, const void *, const void *, const void *,
+                            int, int, int, int, cudaStream_t, int, const void *>;
+std::mutex g_graph_mu;
+std::list<std::pair<GraphKey, cudaGraphExec_t>> g_graphs;   // most recent first
+constexpr size_t kMaxGraphs = 32;
+
+// ---------------------------------------------------------------- decoding
+struct Group {
+  polar_frozen_set *fs;
+  int nframes;
+  const float *llr;
+  const uint32_t *fv;
+  uint32_t *xhat;
+  uint32_t *uhat;
+  int fkind, prec;
+};
+
+struct Exec {
+  const Plan *plan;
+  const Group *g;
+  const uint32_t *dmask;
+  void *ws;
+  int n, t;
+};
+
+inline void *level_ptr(const Exec &x, int k) {
+  // levels t .. n-1 of all frames: level k at F * (2^k - 2^t) elements
+  size_t off = (size_t)x.g->nframes * ((size_t(1) << k) - (size_t(1) << x.t));
+  return static_cast<char *>(x.ws) + off * storage_bytes(x.g->prec);
+}
+
+int run_ops(const Exec &x, cudaStream_t s) {
+  const Group &g = *x.g;
+  const int n = x.n, t = x.t;
+  const uint64_t N = uint64_t(1) << n;
+  const size_t W = N >= 32 ? N / 32 : 1;
+  for (const Op &op : x.plan->ops) {
+    switch (op.kind) {
+      case OP_F:
+      case OP_G: {
+        const int k = op.k;
+        const bool top = (k == n);
+        const void *in = top ? static_cast<const void *>(g.llr) : level_ptr(x, k);
+        const size_t ins = top ? N : (size_t(1) << k);
+        void *out = level_ptr(x, k - 1);
+        const uint64_t h = uint64_t(1) << (k - 1);
+        if (op.kind == OP_F) {
+          CK(launch_stream_f(g.prec, g.fkind, in, ins, top, out, h, h, g.nframes, s));
+        } else {
+          CK(launch_stream_g(g.prec, in, ins, top, out, h, h, g.xhat, W, op.o, g.nframes, s));
+        }
+        break;
+      }
+      case OP_ST: {
+        SubtreeArgs a;
+        a.in_is_llr = (n == t);
+        a.in = a.in_is_llr ? static_cast<const void *>(g.llr) : level_ptr(x, t);
+        a.in_stride = a.in_is_llr ? N : (size_t(1) << t);
+        a.mask = x.dmask;
+        a.fv = g.fv;
+        a.xhat = g.xhat;
+        a.uhat = g.uhat;
+        a.w_stride = W;
+        a.o = op.o;
+        a.t = t;
+        a.r = op.r;
+        a.nframes = g.nframes;
+        a.fkind = g.fkind;
+        a.prec = g.prec;
+        a.shortcuts = x.plan->shortcuts;
+        CK(launch_subtree(a, s));
+        break;
+      }
+      case OP_R0: {
+        const size_t off = op.o >> 5, nw = size_t(1) << (op.k - 5);
+        CK(launch_copy_regions(g.fv, g.xhat, W, off, nw, g.nframes, nullptr, s));
+        if (g.uhat) CK(launch_copy_regions(g.fv, g.uhat, W, off, nw, g.nframes, nullptr, s));
+        CK(launch_encode_regions(g.xhat, W, off, op.k, g.nframes, s));
+        CK(launch_cascade(g.xhat, W, op.k, op.o, op.r, g.nframes, s));
+        break;
+      }
+    }
+  }
+  return POLAR_OK;
+}
+
+int current_device(int *dev) {
+  cudaError_t e = cudaGetDevice(dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return POLAR_OK;
+}
+
+int decode_group(const Group &g, cudaStream_t s) {
+  polar_frozen_set *fs = g.fs;
+  const int n = (int)fs->log2n;
+  const bool plain = g_cfg.plain.load() != 0;
+  const bool shortcuts = !plain && g_cfg.shortcuts.load() != 0;
+  const bool graphs = !plain && g_cfg.graphs.load() != 0;
+  const int t = std::min<int>(n, (int)g_cfg.subtree_log2.load());
+  int dev = 0;
+  int rc = current_device(&dev);
+  if (rc) return rc;
+  cudaError_t e;
+  const uint32_t *dmask = device_mask(fs, dev, &e);
+  if (!dmask) return e == cudaErrorMemoryAllocation ? POLAR_ENOMEM : cuda_fail(e);
+  std::shared_ptr<Plan> plan = get_plan(fs, t, shortcuts);
+  const int F = plain ? 1 : g.nframes;
+  size_t ws_bytes = n > t ? (size_t)F * ((size_t(1) << n) - (size_t(1) << t)) * storage_bytes(g.prec)
+                          : 0;
+  void *ws = nullptr;
+  if (ws_bytes) {
+    rc = get_workspace(dev, s, ws_bytes, &ws);
+    if (rc) return rc;
+  }
+  if (plain) {
+    const uint64_t N = uint64_t(1) << n;
+    const size_t W = N >= 32 ? N / 32 : 1;
+    for (int f = 0; f < g.nframes; ++f) {
+      Group one = g;
+      one.nframes = 1;
+      one.llr = g.llr + (size_t)f * N;
+      one.fv = g.fv + (size_t)f * W;
+      one.xhat = g.xhat + (size_t)f * W;
+      one.uhat = g.uhat ? g.uhat + (size_t)f * W : nullptr;
+      Exec x{plan.get(), &one, dmask, ws, n, t};
+      rc = run_ops(x, s);
+      if (rc) return rc;
+    }
+    return POLAR_OK;
+  }
+  Exec x{plan.get(), &g, dmask, ws, n, t};
+  bool use_graph = graphs && s != nullptr;
+  if (use_graph) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) use_graph = false;   // caller is capturing
+  }
+  if (!use_graph) return run_ops(x, s);
+
+  GraphKey key{fs->id, g.nframes, g.llr, g.fv, g.xhat, g.uhat, g.fkind, g.prec, t,
+               shortcuts ? 1 : 0, s, dev, ws};
+  cudaGraphExec_t exec = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    for (auto it = g_graphs.begin(); it != g_graphs.end(); ++it) {
+      if (it->first == key) {
+        exec = it->second;
+        g_graphs.splice(g_graphs.begin(), g_graphs, it);
+        break;
+      }
+    }
+  }
+  if (!exec) {
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    rc = run_ops(x, s);
+    cudaGraph_t graph = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(s, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (ee != cudaSuccess) return cuda_fail(ee);
+    ee = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ee != cudaSuccess) return cuda_fail(ee);
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    g_graphs.emplace_front(key, exec);
+    if (g_graphs.size() > kMaxGraphs) {
+      cudaGraphExecDestroy(g_graphs.back().second);
+      g_graphs.pop_back();
+    }
+  }
+  CK(cudaGraphLaunch(exec, s));
+  return POLAR_OK;
+}
+
+int check_group(const Group &g) {
+  if (!g.fs || g.nframes < 1 || !g.llr || !g.fv || !g.xhat) return POLAR_EINVAL;
+  if (g.fkind != POLAR_F_MINSUM && g.fkind != POLAR_F_EXACT) return POLAR_EINVAL;
+  if (g.prec != POLAR_FP32 && g.prec != POLAR_FP16) return POLAR_EINVAL;
+  if (!aligned(g.llr, 16) || !aligned(g.fv, 4) || !aligned(g.xhat, 4)) return POLAR_EINVAL;
+  if (g.uhat && !aligned(g.uhat, 4)) return POLAR_EINVAL;
+  return POLAR_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+const char *polar_strerror(int status) {
+  switch (status) {
+    case POLAR_OK: return "ok";
+    case POLAR_EINVAL: return "invalid argument";
+    case POLAR_ENOMEM: return "out of memory";
+    case POLAR_ECUDA: return "CUDA error";
+    case POLAR_ETIMEDOUT: return "device wait timed out";
+    case POLAR_EBUSY: return "admission refused";
+    case POLAR_ENOTFOUND: return "not found";
+    case POLAR_PENDING: return "pending";
+    default: return "unknown status";
+  }
+}
+
+const char *polar_last_error_string(void) { return g_last_error.c_str(); }
+
+int polar_config_set(const char *key, long value) {
+  if (!key) return POLAR_EINVAL;
+  if (!strcmp(key, "subtree_log2")) {
+    if (value < 5 || value > 14) return POLAR_EINVAL;
+    g_cfg.subtree_log2 = value;
+  } else if (!strcmp(key, "shortcuts")) {
+    g_cfg.shortcuts = value ? 1 : 0;
+  } else if (!strcmp(key, "graphs")) {
+    g_cfg.graphs = value ? 1 : 0;
+  } else if (!strcmp(key, "plain")) {
+    g_cfg.plain = value ? 1 : 0;
+  } else {
+    return POLAR_ENOTFOUND;
+  }
+  return POLAR_OK;
+}
+
+int polar_config_get(const char *key, long *value) {
+  if (!key || !value) return POLAR_EINVAL;
+  if (!strcmp(key, "subtree_log2")) *value = g_cfg.subtree_log2;
+  else if (!strcmp(key, "shortcuts")) *value = g_cfg.shortcuts;
+  else if (!strcmp(key, "graphs")) *value = g_cfg.graphs;
+  else if (!strcmp(key, "plain")) *value = g_cfg.plain;
+  else return POLAR_ENOTFOUND;
+  return POLAR_OK;
+}
+
+int polar_build_frozen_set(uint32_t log2n, polar_channel ch, double param, double rate,
+                           polar_frozen_set **out) {
+  return build_frozen_set(log2n, ch, param, rate, out);
+}
+
+int polar_frozen_set_from_mask(uint32_t log2n, const uint32_t *mask_host,
+                               polar_frozen_set **out) {
+  return frozen_set_from_mask(log2n, mask_host, out);
+}
+
+int polar_frozen_set_query(const polar_frozen_set *fs, uint32_t *log2n, uint64_t *k,
+                           uint32_t *mask_host, double *sum_pe_info) {
+  if (!fs) return POLAR_EINVAL;
+  if (log2n) *log2n = fs->log2n;
+  if (k) *k = fs->K;
+  if (mask_host) std::memcpy(mask_host, fs->mask.data(), fs->mask.size() * sizeof(uint32_t));
+  if (sum_pe_info) *sum_pe_info = fs->sum_pe;
+  return POLAR_OK;
+}
+
+void polar_frozen_set_free(polar_frozen_set *fs) {
+  if (!fs) return;
+  {
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    for (auto it = g_graphs.begin(); it != g_graphs.end();) {
+      if (std::get<0>(it->first) == fs->id) {
+        cudaGraphExecDestroy(it->second);
+        it = g_graphs.erase(it);
+      } else {
+        ++it;
+      }
+    }
+  }
+  for (auto &kv : fs->dmask) cudaFree(kv.second);
+  delete fs;
+}
+
+int polar_llr_from_channel(polar_channel ch, double param, const void *y_dev, int y_is_bits,
+                           float *llr_dev, size_t n_total, void *stream) {
+  if (!y_dev || !llr_dev) return POLAR_EINVAL;
+  if (n_total == 0) return POLAR_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (ch == POLAR_BSC) {
+    if (!y_is_bits || !(param > 0.0 && param < 0.5) || n_total % 32) return POLAR_EINVAL;
+    if (!aligned(y_dev, 4) || !aligned(llr_dev, 16)) return POLAR_EINVAL;
+    const float c = (float)std::log((1.0 - param) / param);
+    CK(launch_llr_bsc(static_cast<const uint32_t *>(y_dev), llr_dev, n_total, c, s));
+    return POLAR_OK;
+  }
+  if (ch == POLAR_BIAWGN) {
+    if (y_is_bits || !(param > 0.0 && std::isfinite(param))) return POLAR_EINVAL;
+    if (!aligned(y_dev, 16) || !aligned(llr_dev, 8)) return POLAR_EINVAL;
+    CK(launch_llr_biawgn(static_cast<const double *>(y_dev), llr_dev, n_total, 2.0 / param, s));
+    return POLAR_OK;
+  }
+  return POLAR_EINVAL;
+}
+
+int polar_encode(uint32_t log2n, int nframes, const uint32_t *in_dev, uint32_t *out_dev,
+                 void *stream) {
+  if (log2n < 1 || log2n > 26 || nframes < 1 || !in_dev || !out_dev) return POLAR_EINVAL;
+  if (!aligned(in_dev, 4) || !aligned(out_dev, 4)) return POLAR_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t W = log2n >= 5 ? (size_t(1) << (log2n - 5)) : 1;
+  if (in_dev != out_dev) CK(launch_copy_regions(in_dev, out_dev, W, 0, W, nframes, nullptr, s));
+  CK(launch_encode_regions(out_dev, W, 0, (int)log2n, nframes, s));
+  return POLAR_OK;
+}
+
+int polar_reveal(const polar_frozen_set *fs_c, int nframes, const uint32_t *x_dev,
+                 uint32_t *fval_dev, void *stream) {
+  if (!fs_c || nframes < 1 || !x_dev || !fval_dev) return POLAR_EINVAL;
+  if (!aligned(x_dev, 4) || !aligned(fval_dev, 4)) return POLAR_EINVAL;
+  polar_frozen_set *fs = const_cast<polar_frozen_set *>(fs_c);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0;
+  int rc = current_device(&dev);
+  if (rc) return rc;
+  cudaError_t e;
+  const uint32_t *dmask = device_mask(fs, dev, &e);
+  if (!dmask) return e == cudaErrorMemoryAllocation ? POLAR_ENOMEM : cuda_fail(e);
+  const size_t W = fs->mask.size();
+  if (x_dev != fval_dev) CK(launch_copy_regions(x_dev, fval_dev, W, 0, W, nframes, nullptr, s));
+  CK(launch_encode_regions(fval_dev, W, 0, (int)fs->log2n, nframes, s));
+  CK(launch_copy_regions(fval_dev, fval_dev, W, 0, W, nframes, dmask, s));
+  return POLAR_OK;
+}
+
+int polar_sc_decode_many(const polar_frozen_set *fs, int nframes, const float *llr_dev,
+                         const uint32_t *frozen_vals_dev, uint32_t *xhat_dev, uint32_t *uhat_dev,
+                         polar_fkind fkind, polar_prec prec, void *stream) {
+  Group g{const_cast<polar_frozen_set *>(fs), nframes, llr_dev, frozen_vals_dev, xhat_dev,
+          uhat_dev, (int)fkind, (int)prec};
+  int rc = check_group(g);
+  if (rc) return rc;
+  return decode_group(g, static_cast<cudaStream_t>(stream));
+}
+
+int polar_sc_decode(const polar_frozen_set *fs, const float *llr_dev,
+                    const uint32_t *frozen_vals_dev, uint32_t *xhat_dev, uint32_t *uhat_dev,
+                    polar_fkind fkind, polar_prec prec, void *stream) {
+  return polar_sc_decode_many(fs, 1, llr_dev, frozen_vals_dev, xhat_dev, uhat_dev, fkind, prec,
+                              stream);
+}
+
+int polar_sc_decode_batch(int nframes, const polar_frame_desc *frames, polar_fkind fkind,
+                          polar_prec prec, void *stream) {
+  if (nframes < 1 || !frames) return POLAR_EINVAL;
+  for (int i = 0; i < nframes; ++i) {
+    Group one{const_cast<polar_frozen_set *>(frames[i].fs), 1, frames[i].llr,
+              frames[i].frozen_vals, frames[i].xhat, frames[i].uhat, (int)fkind, (int)prec};
+    int rc = check_group(one);
+    if (rc) return rc;
+  }
+  int i = 0;
+  while (i < nframes) {
+    const polar_frame_desc &a = frames[i];
+    const uint64_t N = a.fs->N;
+    const size_t W = a.fs->mask.size();
+    int j = i + 1;
+    while (j < nframes) {
+      const polar_frame_desc &b = frames[j];
+      const size_t d = (size_t)(j - i);
+      if (b.fs != a.fs || b.llr != a.llr + d * N || b.frozen_vals != a.frozen_vals + d * W ||
+          b.xhat != a.xhat + d * W || (a.uhat == nullptr) != (b.uhat == nullptr) ||
+          (a.uhat && b.uhat != a.uhat + d * W))
+        break;
+      ++j;
+    }
+    Group g{const_cast<polar_frozen_set *>(a.fs), j - i, a.llr, a.frozen_vals, a.xhat, a.uhat,
+            (int)fkind, (int)prec};
+    int rc = decode_group(g, static_cast<cudaStream_t>(stream));
+    if (rc) return rc;
+    i = j;
+  }
+  return POLAR_OK;
+}
+
+}  // extern "C"

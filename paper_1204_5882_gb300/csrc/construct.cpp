@@ -1,0 +1,284 @@
+// Frozen-set construction on the host (Sec. 3: the frozen bits are the
+// bit-channels of lowest capacity found by density evolution; equal
+// reliabilities freeze the lower index first).
+//
+// Reliability measures, in double precision and in the log domain so that
+// nothing underflows up to N = 2^26:
+//   BSC     Bhattacharyya recursion  ln Z- = ln Z + ln(2 - Z),  ln Z+ = 2 ln Z,
+//           ln Z0 = ln 2 + (ln p + ln(1 - p)) / 2;
+//   BIAWGN  Gaussian approximation of density evolution (Chung, Richardson,
+//           Urbanke 2001): m0 = 2 / sigma^2, m+ = 2 m,
+//           m- = phi^-1(1 - (1 - phi(m))^2),  P_e = Q(sqrt(m / 2)).
+// The first polarisation step sets the most significant index bit, which is
+// the top split of the natural-order decoder.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <thread>
+
+#include "polar_internal.h"
+
+namespace polar {
+
+static std::atomic<uint64_t> g_fs_ids{1};
+
+// ---------------------------------------------------------------- BSC
+static inline double bh_step(double lz, bool plus) {
+  if (plus) return 2.0 * lz;
+  return lz + std::log1p(-std::expm1(lz));   // ln(2Z - Z^2)
+}
+
+// ---------------------------------------------------------------- GA
+// ln phi_GA(x): exp(-0.4527 x^0.86 + 0.0218) below 10, the asymptotic form
+// sqrt(pi/x) e^{-x/4} (1 - 10/(7x)) from 10 on.
+static inline double ga_lnphi(double x) {
+  if (x < 10.0) return -0.4527 * std::pow(x, 0.86) + 0.0218;
+  return 0.5 * std::log(M_PI / x) - 0.25 * x + std::log1p(-10.0 / (7.0 * x));
+}
+
+// d/dx ln phi_GA on the x >= 10 piece.
+static inline double ga_dlnphi_hi(double x) {
+  double a = 10.0 / (7.0 * x);
+  return -0.5 / x - 0.25 + (a / x) / (1.0 - a);
+}
+
+// Inverse of ln phi_GA.  The two pieces do not meet at x = 10 (ln phi jumps
+// up from -3.2576 to -3.2331), so targets in that gap have two preimages;
+// the x < 10 piece is taken whenever its range holds the target.  On the
+// x >= 10 piece the result is the smallest double x with ln phi(x) <= t,
+// found by Newton steps from x ~ -4t and finished by ulp steps.
+static double ga_lnphi_inv(double t) {
+  const double left10 = -0.4527 * std::pow(10.0, 0.86) + 0.0218;
+  if (t > left10) {
+    double v = (0.0218 - t) / 0.4527;
+    return v > 0.0 ? std::pow(v, 1.0 / 0.86) : 0.0;
+  }
+  double lo = 10.0, hi = std::max(20.0, -8.0 * t);
+  while (ga_lnphi(hi) > t) hi *= 2.0;
+  double x = std::min(std::max(-4.0 * t, lo), hi);
+  for (int it = 0; it < 100; ++it) {
+    double fx = ga_lnphi(x) - t;
+    if (fx > 0) lo = x; else hi = x;
+    double nx = x - fx / ga_dlnphi_hi(x);
+    if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
+    if (nx == x) break;
+    x = nx;
+    if (hi - lo <= 4.0 * std::nextafter(hi, INFINITY) - 4.0 * hi) break;
+  }
+  // smallest double with ln phi(x) <= t
+  while (ga_lnphi(x) > t) x = std::nextafter(x, INFINITY);
+  for (;;) {
+    double p = std::nextafter(x, 0.0);
+    if (p < 10.0 || ga_lnphi(p) > t) break;
+    x = p;
+  }
+  return x;
+}
+
+static inline double ga_step(double m, bool plus) {
+  if (plus) return 2.0 * m;
+  double lp = ga_lnphi(m);
+  return ga_lnphi_inv(lp + std::log1p(-std::expm1(lp)));   // ln(phi (2 - phi))
+}
+
+// ln Q(x), x >= 0.
+static inline double ln_q(double x) {
+  if (x < 30.0) return std::log(0.5 * std::erfc(x / M_SQRT2));
+  double x2 = x * x;
+  double s = 1.0 - 1.0 / x2 + 3.0 / (x2 * x2) - 15.0 / (x2 * x2 * x2);
+  return -0.5 * x2 - std::log(x) - 0.5 * std::log(2.0 * M_PI) + std::log(s);
+}
+
+// Expand the one-channel parameter into 2^n bit-channel parameters, level by
+// level, in place from the top down (children 2j <- minus, 2j+1 <- plus).
+template <class Step>
+static void polarise(std::vector<double> &v, uint32_t n, Step step) {
+  for (uint32_t s = 0; s < n; ++s) {
+    size_t len = size_t(1) << s;
+    if (len >= 4096) {
+      // parallel over disjoint chunks, each written from its end backwards
+      unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+      std::vector<double> tmp(2 * len);
+      std::vector<std::thread> th;
+      for (unsigned w = 0; w < nt; ++w)
+        th.emplace_back([&, w] {
+          size_t a = len * w / nt, b = len * (w + 1) / nt;
+          for (size_t j = a; j < b; ++j) {
+            tmp[2 * j] = step(v[j], false);
+            tmp[2 * j + 1] = step(v[j], true);
+          }
+        });
+      for (auto &x : th) x.join();
+      std::copy(tmp.begin(), tmp.end(), v.begin());
+    } else {
+      for (size_t j = len; j-- > 0;) {
+        double p = v[j];
+        v[2 * j + 1] = step(p, true);
+        v[2 * j] = step(p, false);
+      }
+    }
+  }
+}
+
+static polar_frozen_set *new_set(uint32_t log2n) {
+  auto *fs = new (std::nothrow) polar_frozen_set();
+  if (!fs) return nullptr;
+  fs->id = g_fs_ids.fetch_add(1);
+  fs->log2n = log2n;
+  fs->N = uint64_t(1) << log2n;
+  fs->mask.assign(std::max<uint64_t>(1, fs->N / 32), 0u);
+  return fs;
+}
+
+int build_frozen_set(uint32_t log2n, polar_channel ch, double param, double rate,
+                     polar_frozen_set **out) {
+  if (!out || log2n < 1 || log2n > 26) return POLAR_EINVAL;
+  if (!(rate >= 0.0 && rate <= 1.0)) return POLAR_EINVAL;
+  if (ch == POLAR_BSC) {
+    if (!(param > 0.0 && param < 0.5)) return POLAR_EINVAL;
+  } else if (ch == POLAR_BIAWGN) {
+    if (!(param > 0.0 && std::isfinite(param))) return POLAR_EINVAL;
+  } else {
+    return POLAR_EINVAL;
+  }
+  const uint64_t N = uint64_t(1) << log2n;
+  std::vector<double> bad;
+  try {
+    bad.assign(N, 0.0);
+  } catch (...) {
+    return POLAR_ENOMEM;
+  }
+  if (ch == POLAR_BSC) {
+    bad[0] = std::log(2.0) + 0.5 * (std::log(param) + std::log1p(-param));
+    polarise(bad, log2n, bh_step);
+  } else {
+    bad[0] = 2.0 / param;
+    polarise(bad, log2n, ga_step);
+    for (auto &m : bad) m = ln_q(std::sqrt(m / 2.0));
+  }
+  polar_frozen_set *fs = new_set(log2n);
+  if (!fs) return POLAR_ENOMEM;
+  fs->K = (uint64_t)std::floor(rate * (double)N);
+  if (fs->K > N) fs->K = N;
+  // Rank by unreliability (descending), lower index first on ties; the
+  // first N-K are frozen.
+  std::vector<uint32_t> idx(N);
+  for (uint64_t i = 0; i < N; ++i) idx[i] = (uint32_t)i;
+  auto worse = [&](uint32_t a, uint32_t b) {
+    if (bad[a] != bad[b]) return bad[a] > bad[b];
+    return a < b;
+  };
+  const uint64_t nf = N - fs->K;
+  if (nf > 0 && nf < N) std::nth_element(idx.begin(), idx.begin() + nf, idx.end(), worse);
+  for (uint64_t r = 0; r < nf; ++r) fs->mask[idx[r] >> 5] |= 1u << (idx[r] & 31);
+  double s = 0.0;
+  for (uint64_t r = nf; r < N; ++r) s += std::exp(bad[idx[r]]);
+  fs->sum_pe = s;
+  *out = fs;
+  return POLAR_OK;
+}
+
+int frozen_set_from_mask(uint32_t log2n, const uint32_t *mask, polar_frozen_set **out) {
+  if (!out || !mask || log2n < 1 || log2n > 26) return POLAR_EINVAL;
+  polar_frozen_set *fs = new_set(log2n);
+  if (!fs) return POLAR_ENOMEM;
+  const uint64_t W = fs->mask.size();
+  uint64_t frozen = 0;
+  for (uint64_t w = 0; w < W; ++w) {
+    uint32_t v = mask[w];
+    if (fs->N < 32) v &= (1u << fs->N) - 1u;
+    fs->mask[w] = v;
+    frozen += (uint64_t)__builtin_popcount(v);
+  }
+  fs->K = fs->N - frozen;
+  fs->sum_pe = std::nan("");
+  *out = fs;
+  return POLAR_OK;
+}
+
+// Class of the node of 2^k leaves starting at leaf o, from the host mask.
+NodeClass node_class_host(const polar_frozen_set *fs, int k, uint64_t o) {
+  if (k < 5) {
+    uint32_t w = fs->mask[o >> 5];
+    uint32_t m = (1u << (1u << k)) - 1u;
+    uint32_t b = (w >> (o & 31)) & m;
+    return b == m ? NODE_RATE0 : (b == 0 ? NODE_RATE1 : NODE_MIXED);
+  }
+  uint64_t w0 = o >> 5, nw = uint64_t(1) << (k - 5);
+  bool all1 = true, all0 = true;
+  for (uint64_t w = w0; w < w0 + nw && (all1 || all0); ++w) {
+    all1 &= fs->mask[w] == 0xFFFFFFFFu;
+    all0 &= fs->mask[w] == 0u;
+  }
+  return all1 ? NODE_RATE0 : (all0 ? NODE_RATE1 : NODE_MIXED);
+}
+
+// Streamed schedule of the SC recursion above level t.  Rate-0 nodes of any
+// size become one OP_R0 (their partial sums are the encoded frozen values,
+// independent of the LLRs); the f feeding a rate-0 left child is skipped.
+// Every unit (subtree or rate-0 node) records how many levels it is a right
+// child for: that many partial-sum combines follow it.
+static void plan_visit(const polar_frozen_set *fs, Plan &p, int k, uint64_t o) {
+  const int n = (int)fs->log2n;
+  auto unit_r = [&](int ku, uint64_t ou) {
+    uint64_t pos = ou >> ku;
+    int r = 0;
+    while (ku + r < n && ((pos >> r) & 1)) ++r;
+    return r;
+  };
+  auto rate0 = [&](int kk, uint64_t oo) {
+    return p.shortcuts && kk >= 5 && node_class_host(fs, kk, oo) == NODE_RATE0;
+  };
+  if (rate0(k, o)) {
+    p.ops.push_back(Op{OP_R0, (uint8_t)k, (uint8_t)unit_r(k, o), 0, o});
+    p.n_r0++;
+    return;
+  }
+  if (k == p.t) {
+    p.ops.push_back(Op{OP_ST, (uint8_t)k, (uint8_t)unit_r(k, o), 0, o});
+    p.n_st++;
+    return;
+  }
+  uint64_t h = uint64_t(1) << (k - 1);
+  if (!rate0(k - 1, o)) {
+    p.ops.push_back(Op{OP_F, (uint8_t)k, 0, 0, o});
+    p.n_f++;
+  }
+  plan_visit(fs, p, k - 1, o);
+  p.ops.push_back(Op{OP_G, (uint8_t)k, 0, 0, o});
+  p.n_g++;
+  plan_visit(fs, p, k - 1, o + h);
+}
+
+std::shared_ptr<Plan> get_plan(polar_frozen_set *fs, int t, bool shortcuts) {
+  std::lock_guard<std::mutex> g(fs->mu);
+  auto key = std::make_pair(t, shortcuts ? 1 : 0);
+  auto it = fs->plans.find(key);
+  if (it != fs->plans.end()) return it->second;
+  auto p = std::make_shared<Plan>();
+  p->t = t;
+  p->shortcuts = shortcuts;
+  plan_visit(fs, *p, (int)fs->log2n, 0);
+  fs->plans[key] = p;
+  return p;
+}
+
+const uint32_t *device_mask(polar_frozen_set *fs, int device, cudaError_t *err) {
+  std::lock_guard<std::mutex> g(fs->mu);
+  *err = cudaSuccess;
+  auto it = fs->dmask.find(device);
+  if (it != fs->dmask.end()) return it->second;
+  uint32_t *d = nullptr;
+  size_t bytes = fs->mask.size() * sizeof(uint32_t);
+  *err = cudaMalloc(&d, bytes);
+  if (*err != cudaSuccess) return nullptr;
+  *err = cudaMemcpy(d, fs->mask.data(), bytes, cudaMemcpyHostToDevice);
+  if (*err != cudaSuccess) {
+    cudaFree(d);
+    return nullptr;
+  }
+  fs->dmask[device] = d;
+  return d;
+}
+
+}  // namespace polar

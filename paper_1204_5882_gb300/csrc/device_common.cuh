@@ -1,0 +1,102 @@
+// Device-side building blocks shared by the streamed and the subtree kernels.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cstdint>
+
+namespace polar {
+
+// ---------------------------------------------------------------- f and g
+// Min-sum check-node update: sign = - iff exactly one input has its sign bit
+// set, magnitude = min(|a|, |b|).  Bit-exact with a float32 recursive SC.
+__device__ __forceinline__ float f_minsum(float a, float b) {
+  float m = fminf(fabsf(a), fabsf(b));
+  uint32_t s = (__float_as_uint(a) ^ __float_as_uint(b)) & 0x80000000u;
+  return __uint_as_float(__float_as_uint(m) | s);
+}
+
+// Exact check-node update f = 2 atanh(tanh(a/2) tanh(b/2)) (Sec. 4's update
+// through phi), evaluated as
+//   sgn(a) sgn(b) [min(A,B) + log1p(e^{-(A+B)}) - log1p(e^{-|A-B|})]
+// which never forms atanh(+-1); the magnitude is clamped at zero because
+// rounding can push it slightly negative for tiny inputs.
+__device__ __forceinline__ float f_exact(float a, float b) {
+  float A = fabsf(a), B = fabsf(b);
+  float m = fminf(A, B) + log1pf(expf(-(A + B))) - log1pf(expf(-fabsf(A - B)));
+  m = fmaxf(m, 0.0f);
+  uint32_t s = (__float_as_uint(a) ^ __float_as_uint(b)) & 0x80000000u;
+  return __uint_as_float(__float_as_uint(m) | s);
+}
+
+template <int FK>
+__device__ __forceinline__ float f_op(float a, float b) {
+  if (FK == 0) return f_minsum(a, b);
+  return f_exact(a, b);
+}
+
+// Variable-node update with the left child's partial sum u: b + a or b - a.
+__device__ __forceinline__ float g_op(float a, float b, uint32_t u) {
+  return u ? (b - a) : (b + a);
+}
+
+// ---------------------------------------------------------------- storage
+// Intermediate LLRs are stored as float, half (round to nearest even,
+// saturated at +-65504) or int8 (round to nearest even, saturated at +-127,
+// values are L * per-frame scale); every f and g runs in float.
+template <typename S>
+struct Store;
+
+template <>
+struct Store<float> {
+  static __device__ __forceinline__ float ld(const float *p) { return *p; }
+  static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
+};
+
+template <>
+struct Store<__half> {
+  static __device__ __forceinline__ float ld(const __half *p) { return __half2float(*p); }
+  static __device__ __forceinline__ void st(__half *p, float v) {
+    *p = __float2half_rn(fminf(fmaxf(v, -65504.0f), 65504.0f));
+  }
+};
+
+template <>
+struct Store<int8_t> {
+  static __device__ __forceinline__ float ld(const int8_t *p) { return (float)*p; }
+  static __device__ __forceinline__ void st(int8_t *p, float v) {
+    *p = (int8_t)fminf(fmaxf(rintf(v), -127.0f), 127.0f);
+  }
+};
+
+// ---------------------------------------------------------------- bits
+// x = u F^{(x)k} on the low 2^k bits of a word (k <= 5): for h = 1, 2, ...,
+// the low half of every block of 2h bits is XORed with its high half.
+__device__ __forceinline__ uint32_t encode_word(uint32_t w, int k) {
+  if (k > 0) w ^= (w >> 1) & 0x55555555u;
+  if (k > 1) w ^= (w >> 2) & 0x33333333u;
+  if (k > 2) w ^= (w >> 4) & 0x0F0F0F0Fu;
+  if (k > 3) w ^= (w >> 8) & 0x00FF00FFu;
+  if (k > 4) w ^= (w >> 16) & 0x0000FFFFu;
+  return w;
+}
+
+__device__ __forceinline__ uint32_t low_mask(int nbits) {
+  return nbits >= 32 ? 0xFFFFFFFFu : ((1u << nbits) - 1u);
+}
+
+// Partial sums live in place in x_hat: a node of 2^k leaves at leaf o keeps
+// its beta in bits [o, o + 2^k).  When a unit of 2^ku leaves at ou finishes as
+// a right child for r levels, each parent (left half ^= right half) is formed
+// in turn by the calling CTA, levels in order (ku >= 5: whole words).
+__device__ __forceinline__ void cascade_device(uint32_t *x, int ku, uint64_t ou, int r) {
+  for (int m = 0; m < r; ++m) {
+    int L = ku + m;
+    uint64_t base = (ou >> (L + 1)) << (L + 1);
+    uint64_t hw = (uint64_t(1) << L) >> 5;
+    uint32_t *left = x + (base >> 5);
+    for (uint64_t i = threadIdx.x; i < hw; i += blockDim.x) left[i] ^= left[hw + i];
+    __syncthreads();
+  }
+}
+
+}  // namespace polar

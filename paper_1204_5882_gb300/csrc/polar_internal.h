@@ -1,0 +1,126 @@
+// Internal declarations of the GB300 SC polar decoder library (not part of
+// the C ABI).  The public contract is include/polar.h.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "polar.h"
+
+namespace polar {
+
+// Node classes of the SC tree, read from the frozen mask (Sec. 3 / Sec. 4):
+// all positions frozen (rate 0), all information (rate 1) or mixed.
+enum NodeClass : uint8_t { NODE_MIXED = 0, NODE_RATE0 = 1, NODE_RATE1 = 2 };
+
+// One step of the streamed (upper) part of the SC recursion.  Levels are
+// counted from the leaves: level k holds nodes of 2^k leaves; the root is at
+// level n.  `o` is the first leaf (bit offset) of the node the op touches.
+enum OpKind : uint8_t {
+  OP_F = 0,   // level k -> k-1, left child LLRs  L'[j] = f(L[j], L[j+h])
+  OP_G = 1,   // level k -> k-1, right child LLRs L'[j] = g(L[j], L[j+h], b[o+j])
+  OP_ST = 2,  // decode the subtree of 2^t leaves at o in one CTA
+  OP_R0 = 3,  // rate-0 node of 2^k leaves at o: partial sums = fv F^{(x)k}
+};
+
+struct Op {
+  uint8_t kind;
+  uint8_t k;
+  uint8_t r;   // partial-sum combine levels done after a unit (ST / R0)
+  uint8_t pad;
+  uint64_t o;
+};
+
+struct Plan {
+  int t = 0;
+  bool shortcuts = true;
+  std::vector<Op> ops;
+  int n_st = 0, n_f = 0, n_g = 0, n_r0 = 0;
+};
+
+}  // namespace polar
+
+struct polar_frozen_set {
+  uint64_t id = 0;
+  uint32_t log2n = 0;
+  uint64_t N = 0, K = 0;
+  double sum_pe = 0.0;
+  std::vector<uint32_t> mask;   // max(1, N/32) words, bit set = frozen
+  std::mutex mu;
+  std::map<int, uint32_t *> dmask;                        // device -> mask copy
+  std::map<std::pair<int, int>, std::shared_ptr<polar::Plan>> plans;  // (t, shortcuts)
+};
+
+namespace polar {
+
+// --- construction (construct.cpp) -----------------------------------------
+int build_frozen_set(uint32_t log2n, polar_channel ch, double param, double rate,
+                     polar_frozen_set **out);
+int frozen_set_from_mask(uint32_t log2n, const uint32_t *mask, polar_frozen_set **out);
+NodeClass node_class_host(const polar_frozen_set *fs, int k, uint64_t o);
+std::shared_ptr<Plan> get_plan(polar_frozen_set *fs, int t, bool shortcuts);
+const uint32_t *device_mask(polar_frozen_set *fs, int device, cudaError_t *err);
+
+// --- kernels (stream_kernels.cu, subtree.cu) --------------------------------
+struct FrameArrays {
+  const float *llr;     // level n, [F][N]
+  const uint32_t *fv;   // [F][W]
+  uint32_t *xhat;       // [F][W]
+  uint32_t *uhat;       // [F][W] or null
+  int nframes;
+  uint32_t log2n;
+};
+
+cudaError_t launch_llr_bsc(const uint32_t *y, float *llr, size_t n_total, float c,
+                           cudaStream_t s);
+cudaError_t launch_llr_biawgn(const double *y, float *llr, size_t n_total, double scale,
+                              cudaStream_t s);
+// In-place transform of nframes regions of 2^log2len bits; region f starts at
+// words + f * stride_w + off_w (word-aligned, log2len >= 5) or is the low
+// 2^log2len bits of words[f * stride_w] (log2len < 5).
+cudaError_t launch_encode_regions(uint32_t *words, size_t stride_w, size_t off_w,
+                                  int log2len, int nframes, cudaStream_t s);
+cudaError_t launch_copy_regions(const uint32_t *src, uint32_t *dst, size_t stride_w,
+                                size_t off_w, size_t nwords, int nframes,
+                                const uint32_t *and_mask, cudaStream_t s);
+cudaError_t launch_cascade(uint32_t *xhat, size_t stride_w, int k_unit, uint64_t o_unit,
+                           int r, int nframes, cudaStream_t s);
+
+// Streamed f / g for levels above the subtree size (templated on storage).
+cudaError_t launch_stream_f(int prec, int fkind, const void *in, size_t in_stride,
+                            bool in_is_llr, void *out, size_t out_stride, uint64_t h,
+                            int nframes, cudaStream_t s);
+cudaError_t launch_stream_g(int prec, const void *in, size_t in_stride, bool in_is_llr,
+                            void *out, size_t out_stride, uint64_t h,
+                            const uint32_t *xhat, size_t xhat_stride_w, uint64_t o,
+                            int nframes, cudaStream_t s);
+
+struct SubtreeArgs {
+  const void *in;        // level-t LLRs of every frame (or the channel LLRs)
+  size_t in_stride;      // elements between frames
+  bool in_is_llr;        // in is the float channel LLR array (level n == t)
+  const uint32_t *mask;  // device frozen mask (whole code)
+  const uint32_t *fv;
+  uint32_t *xhat;
+  uint32_t *uhat;
+  size_t w_stride;       // words per frame
+  uint64_t o;            // first leaf of the subtree
+  int t;                 // subtree log2 size
+  int r;                 // combine levels after the subtree
+  int nframes;
+  int fkind;
+  int prec;
+  bool shortcuts;
+};
+cudaError_t launch_subtree(const SubtreeArgs &a, cudaStream_t s);
+
+size_t storage_bytes(int prec);
+
+}  // namespace polar

@@ -1,0 +1,312 @@
+// Streamed kernels: channel LLR map, the f and g of levels above the subtree
+// size (long vectors through HBM), the transform on packed bits, and the
+// partial-sum combines.  All are grid-stride, 128-bit where the data allows.
+#include "device_common.cuh"
+#include "polar_internal.h"
+
+namespace polar {
+
+static inline int grid_for(size_t work, int block, int max_blocks = 152 * 16) {
+  size_t g = (work + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > (size_t)max_blocks) g = max_blocks;
+  return (int)g;
+}
+
+// ---------------------------------------------------------------- LLR maps
+// BSC (Sec. 1): L = y ? -c : c; one float4 per thread (4 bits of y).
+__global__ void k_llr_bsc(const uint32_t *__restrict__ y, float4 *__restrict__ llr,
+                          size_t n4, float c) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4;
+       i += (size_t)gridDim.x * blockDim.x) {
+    uint32_t b = (y[i >> 3] >> ((i & 7) * 4)) & 0xFu;
+    float4 v;
+    v.x = (b & 1u) ? -c : c;
+    v.y = (b & 2u) ? -c : c;
+    v.z = (b & 4u) ? -c : c;
+    v.w = (b & 8u) ? -c : c;
+    llr[i] = v;
+  }
+}
+
+// BI-AWGN (Sec. 2.2): L = float(y * (2 / sigma^2)), product in double.
+__global__ void k_llr_biawgn(const double2 *__restrict__ y, float2 *__restrict__ llr,
+                             size_t n2, double s) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2;
+       i += (size_t)gridDim.x * blockDim.x) {
+    double2 v = y[i];
+    llr[i] = make_float2((float)(v.x * s), (float)(v.y * s));
+  }
+}
+
+__global__ void k_llr_biawgn_tail(const double *__restrict__ y, float *__restrict__ llr,
+                                  size_t first, size_t n, double s) {
+  size_t i = first + blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) llr[i] = (float)(y[i] * s);
+}
+
+cudaError_t launch_llr_bsc(const uint32_t *y, float *llr, size_t n_total, float c,
+                           cudaStream_t s) {
+  size_t n4 = n_total / 4;
+  k_llr_bsc<<<grid_for(n4, 256), 256, 0, s>>>(y, reinterpret_cast<float4 *>(llr), n4, c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_llr_biawgn(const double *y, float *llr, size_t n_total, double scale,
+                              cudaStream_t s) {
+  size_t n2 = n_total / 2;
+  if (n2) {
+    k_llr_biawgn<<<grid_for(n2, 256), 256, 0, s>>>(reinterpret_cast<const double2 *>(y),
+                                                  reinterpret_cast<float2 *>(llr), n2, scale);
+  }
+  if (n_total & 1) k_llr_biawgn_tail<<<1, 32, 0, s>>>(y, llr, n2 * 2, n_total, scale);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- transform
+// Region r of nregions covers words [base + r*stride, +nw) (nw = 2^(k-5)).
+__global__ void k_encode_inword(uint32_t *__restrict__ w, size_t stride, size_t off,
+                                size_t nw, int nregions, int k) {
+  size_t total = nw * (size_t)nregions;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    size_t r = i / nw, j = i - r * nw;
+    uint32_t *p = w + r * stride + off + j;
+    if (k >= 5) {
+      *p = encode_word(*p, 5);
+    } else {
+      uint32_t m = low_mask(1 << k);
+      uint32_t v = *p;
+      *p = (v & ~m) | (encode_word(v & m, k) & m);
+    }
+  }
+}
+
+// Cross-word levels 0 .. lv-1 of blocks of 2^lv consecutive words, in shared
+// memory (one block per CTA).  Block b of the region grid covers
+// words [r*stride + off + b*2^lv, +2^lv).
+__global__ void k_encode_xword_smem(uint32_t *__restrict__ w, size_t stride, size_t off,
+                                    size_t nw, int nregions, int lv) {
+  extern __shared__ uint32_t sm[];
+  const size_t bw = size_t(1) << lv;
+  const size_t blocks_per_region = nw / bw;
+  const size_t total = blocks_per_region * (size_t)nregions;
+  for (size_t b = blockIdx.x; b < total; b += gridDim.x) {
+    size_t r = b / blocks_per_region, bb = b - r * blocks_per_region;
+    uint32_t *p = w + r * stride + off + bb * bw;
+    for (size_t i = threadIdx.x; i < bw; i += blockDim.x) sm[i] = p[i];
+    __syncthreads();
+    for (size_t hw = 1; hw < bw; hw <<= 1) {
+      for (size_t i = threadIdx.x; i < bw / 2; i += blockDim.x) {
+        size_t a = ((i / hw) * 2 * hw) + (i % hw);
+        sm[a] ^= sm[a + hw];
+      }
+      __syncthreads();
+    }
+    for (size_t i = threadIdx.x; i < bw; i += blockDim.x) p[i] = sm[i];
+    __syncthreads();
+  }
+}
+
+// One cross-word level: word a ^= word a + hw for a with bit hw clear.
+__global__ void k_encode_xword_level(uint32_t *__restrict__ w, size_t stride, size_t off,
+                                     size_t nw, int nregions, size_t hw) {
+  size_t half = nw / 2;
+  size_t total = half * (size_t)nregions;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    size_t r = i / half, j = i - r * half;
+    size_t a = ((j / hw) * 2 * hw) + (j % hw);
+    uint32_t *p = w + r * stride + off;
+    p[a] ^= p[a + hw];
+  }
+}
+
+cudaError_t launch_encode_regions(uint32_t *words, size_t stride_w, size_t off_w, int log2len,
+                                  int nframes, cudaStream_t s) {
+  size_t nw = log2len >= 5 ? (size_t(1) << (log2len - 5)) : 1;
+  k_encode_inword<<<grid_for(nw * nframes, 256), 256, 0, s>>>(words, stride_w, off_w, nw,
+                                                              nframes, log2len);
+  if (nw > 1) {
+    int lvw = log2len - 5;
+    int lv = lvw < 12 ? lvw : 12;
+    size_t bw = size_t(1) << lv;
+    size_t nblocks = (nw / bw) * nframes;
+    int grid = (int)(nblocks < 4096 ? nblocks : 4096);
+    k_encode_xword_smem<<<grid, 256, bw * sizeof(uint32_t), s>>>(words, stride_w, off_w, nw,
+                                                                 nframes, lv);
+    for (int l = lv; l < lvw; ++l) {
+      size_t hw = size_t(1) << l;
+      k_encode_xword_level<<<grid_for(nw / 2 * nframes, 256), 256, 0, s>>>(
+          words, stride_w, off_w, nw, nframes, hw);
+    }
+  }
+  return cudaGetLastError();
+}
+
+// dst[f][off + j] = src[f][off + j] (& and_mask[off + j] if given).
+__global__ void k_copy_regions(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
+                               size_t stride, size_t off, size_t nw, int nregions,
+                               const uint32_t *__restrict__ and_mask) {
+  size_t total = nw * (size_t)nregions;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    size_t r = i / nw, j = i - r * nw;
+    uint32_t v = src[r * stride + off + j];
+    if (and_mask) v &= and_mask[off + j];
+    dst[r * stride + off + j] = v;
+  }
+}
+
+cudaError_t launch_copy_regions(const uint32_t *src, uint32_t *dst, size_t stride_w,
+                                size_t off_w, size_t nwords, int nframes,
+                                const uint32_t *and_mask, cudaStream_t s) {
+  k_copy_regions<<<grid_for(nwords * nframes, 256), 256, 0, s>>>(src, dst, stride_w, off_w,
+                                                                 nwords, nframes, and_mask);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- combine
+// One CTA per frame; see cascade_device.
+__global__ void k_cascade(uint32_t *__restrict__ xhat, size_t stride, int ku, uint64_t ou,
+                          int r) {
+  cascade_device(xhat + blockIdx.x * stride, ku, ou, r);
+}
+
+cudaError_t launch_cascade(uint32_t *xhat, size_t stride_w, int k_unit, uint64_t o_unit, int r,
+                           int nframes, cudaStream_t s) {
+  if (r <= 0) return cudaSuccess;
+  k_cascade<<<nframes, 512, 0, s>>>(xhat, stride_w, k_unit, o_unit, r);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- stream f / g
+// Level k -> k-1 for every frame: out[j] = f(in[j], in[j+h]) or
+// g(in[j], in[j+h], beta[o+j]), j < h.  grid.y = frame; each thread handles
+// 4 consecutive j per step.
+template <typename Tin, typename Tout, int FK>
+__global__ void k_stream_f(const Tin *__restrict__ in, size_t in_stride, Tout *__restrict__ out,
+                           size_t out_stride, uint64_t h) {
+  const Tin *a = in + blockIdx.y * in_stride;
+  const Tin *b = a + h;
+  Tout *o = out + blockIdx.y * out_stride;
+  const uint64_t h4 = h >> 2;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < h4;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    if constexpr (sizeof(Tin) == 4 && sizeof(Tout) == 4) {
+      float4 x = reinterpret_cast<const float4 *>(a)[i];
+      float4 y = reinterpret_cast<const float4 *>(b)[i];
+      float4 z;
+      z.x = f_op<FK>(x.x, y.x);
+      z.y = f_op<FK>(x.y, y.y);
+      z.z = f_op<FK>(x.z, y.z);
+      z.w = f_op<FK>(x.w, y.w);
+      reinterpret_cast<float4 *>(o)[i] = z;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        uint64_t j = 4 * i + c;
+        Store<Tout>::st(o + j, f_op<FK>(Store<Tin>::ld(a + j), Store<Tin>::ld(b + j)));
+      }
+    }
+  }
+}
+
+template <typename Tin, typename Tout>
+__global__ void k_stream_g(const Tin *__restrict__ in, size_t in_stride, Tout *__restrict__ out,
+                           size_t out_stride, uint64_t h, const uint32_t *__restrict__ xhat,
+                           size_t x_stride, uint64_t o_bits) {
+  const Tin *a = in + blockIdx.y * in_stride;
+  const Tin *b = a + h;
+  Tout *o = out + blockIdx.y * out_stride;
+  const uint32_t *beta = xhat + blockIdx.y * x_stride + (o_bits >> 5);
+  const uint64_t h4 = h >> 2;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < h4;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t bits = (beta[i >> 3] >> ((i & 7) * 4)) & 0xFu;
+    if constexpr (sizeof(Tin) == 4 && sizeof(Tout) == 4) {
+      float4 x = reinterpret_cast<const float4 *>(a)[i];
+      float4 y = reinterpret_cast<const float4 *>(b)[i];
+      float4 z;
+      z.x = g_op(x.x, y.x, bits & 1u);
+      z.y = g_op(x.y, y.y, bits & 2u);
+      z.z = g_op(x.z, y.z, bits & 4u);
+      z.w = g_op(x.w, y.w, bits & 8u);
+      reinterpret_cast<float4 *>(o)[i] = z;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        uint64_t j = 4 * i + c;
+        Store<Tout>::st(o + j,
+                        g_op(Store<Tin>::ld(a + j), Store<Tin>::ld(b + j), (bits >> c) & 1u));
+      }
+    }
+  }
+}
+
+static dim3 stream_grid(uint64_t h, int nframes) {
+  uint64_t h4 = h >> 2;
+  uint64_t want = (h4 + 255) / 256;
+  uint64_t cap = (uint64_t)(152 * 8 + nframes - 1) / nframes;   // ~8 CTAs/SM overall
+  if (cap < 1) cap = 1;
+  if (want > cap) want = cap;
+  if (want < 1) want = 1;
+  return dim3((unsigned)want, (unsigned)nframes);
+}
+
+template <typename T>
+static cudaError_t stream_f_t(int fkind, const void *in, size_t in_stride, bool in_is_llr,
+                              void *out, size_t out_stride, uint64_t h, int nframes,
+                              cudaStream_t s) {
+  dim3 g = stream_grid(h, nframes);
+  if (in_is_llr) {
+    if (fkind == 0)
+      k_stream_f<float, T, 0><<<g, 256, 0, s>>>((const float *)in, in_stride, (T *)out,
+                                                out_stride, h);
+    else
+      k_stream_f<float, T, 1><<<g, 256, 0, s>>>((const float *)in, in_stride, (T *)out,
+                                                out_stride, h);
+  } else {
+    if (fkind == 0)
+      k_stream_f<T, T, 0><<<g, 256, 0, s>>>((const T *)in, in_stride, (T *)out, out_stride, h);
+    else
+      k_stream_f<T, T, 1><<<g, 256, 0, s>>>((const T *)in, in_stride, (T *)out, out_stride, h);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t stream_g_t(const void *in, size_t in_stride, bool in_is_llr, void *out,
+                              size_t out_stride, uint64_t h, const uint32_t *xhat,
+                              size_t xs, uint64_t o, int nframes, cudaStream_t s) {
+  dim3 g = stream_grid(h, nframes);
+  if (in_is_llr)
+    k_stream_g<float, T><<<g, 256, 0, s>>>((const float *)in, in_stride, (T *)out, out_stride, h,
+                                           xhat, xs, o);
+  else
+    k_stream_g<T, T><<<g, 256, 0, s>>>((const T *)in, in_stride, (T *)out, out_stride, h, xhat,
+                                       xs, o);
+  return cudaGetLastError();
+}
+
+size_t storage_bytes(int prec) { return prec == POLAR_FP32 ? 4 : (prec == POLAR_FP16 ? 2 : 1); }
+
+cudaError_t launch_stream_f(int prec, int fkind, const void *in, size_t in_stride,
+                            bool in_is_llr, void *out, size_t out_stride, uint64_t h,
+                            int nframes, cudaStream_t s) {
+  if (prec == POLAR_FP16)
+    return stream_f_t<__half>(fkind, in, in_stride, in_is_llr, out, out_stride, h, nframes, s);
+  return stream_f_t<float>(fkind, in, in_stride, in_is_llr, out, out_stride, h, nframes, s);
+}
+
+cudaError_t launch_stream_g(int prec, const void *in, size_t in_stride, bool in_is_llr,
+                            void *out, size_t out_stride, uint64_t h, const uint32_t *xhat,
+                            size_t xhat_stride_w, uint64_t o, int nframes, cudaStream_t s) {
+  if (prec == POLAR_FP16)
+    return stream_g_t<__half>(in, in_stride, in_is_llr, out, out_stride, h, xhat, xhat_stride_w,
+                              o, nframes, s);
+  return stream_g_t<float>(in, in_stride, in_is_llr, out, out_stride, h, xhat, xhat_stride_w, o,
+                           nframes, s);
+}
+
+}  // namespace polar

@@ -1,0 +1,285 @@
+// In-CTA subtree decoder: one warp runs the SC recursion (Sec. 4) over a
+// node of 2^t leaves whose LLRs sit in shared memory, one CTA per frame.
+//
+// Shared memory: level k of the recursion (2^k LLRs) lives at L[2^k, 2^(k+1)),
+// level t (the input) at L[2^t, 2^(t+1)); bit vectors beta (partial sums, in
+// place), u_hat, the frozen mask and the frozen values take 2^t bits each.
+//
+// Node shortcuts (when enabled) return the exact SC result:
+//   rate 0 (all frozen): beta = fv F^{(x)k} -- SC decides every leaf from fv
+//                        and beta is the transform of the decisions;
+//   rate 1 (all info):   beta = hard(L) when no input LLR is +-0 -- by
+//                        induction f(a, b) has the sign product and g then
+//                        reproduces sgn(b), so each leaf's decision is the
+//                        hard decision of its input; a zero input falls back
+//                        to the full recursion.
+#include "device_common.cuh"
+#include "polar_internal.h"
+
+namespace polar {
+
+namespace {
+
+constexpr uint32_t FULL = 0xFFFFFFFFu;
+
+struct StParams {
+  const void *in;
+  size_t in_stride;
+  const uint32_t *mask;
+  const uint32_t *fv;
+  uint32_t *xhat;
+  uint32_t *uhat;
+  size_t w_stride;
+  uint64_t o;
+  int t;
+  int r;
+};
+
+template <typename S>
+struct Warp {
+  S *L;
+  uint32_t *beta, *uh, *msk, *fvw;
+  int lane;
+
+  __device__ __forceinline__ S *lvl(int k) const { return L + (1u << k); }
+
+  __device__ int node_class(int k, uint32_t o) const {
+    if (k < 5) {
+      uint32_t m = low_mask(1 << k);
+      uint32_t b = (msk[o >> 5] >> (o & 31)) & m;
+      return b == m ? NODE_RATE0 : (b == 0 ? NODE_RATE1 : NODE_MIXED);
+    }
+    uint32_t nw = 1u << (k - 5), w0 = o >> 5;
+    bool all1 = true, all0 = true;
+    for (uint32_t i = lane; i < nw; i += 32) {
+      uint32_t v = msk[w0 + i];
+      all1 &= (v == FULL);
+      all0 &= (v == 0u);
+    }
+    all1 = __all_sync(FULL, all1);
+    all0 = __all_sync(FULL, all0);
+    return all1 ? NODE_RATE0 : (all0 ? NODE_RATE1 : NODE_MIXED);
+  }
+
+  // Cross-word transform levels of the words [w0, w0 + nw) of `v`.
+  __device__ void xword_encode(uint32_t *v, uint32_t w0, uint32_t nw) const {
+    for (uint32_t hw = 1; hw < nw; hw <<= 1) {
+      __syncwarp();
+      for (uint32_t j = lane; j < nw / 2; j += 32) {
+        uint32_t a = (j / hw) * 2 * hw + (j % hw);
+        v[w0 + a] ^= v[w0 + a + hw];
+      }
+    }
+    __syncwarp();
+  }
+
+  __device__ void insert(uint32_t *v, uint32_t o, int nbits, uint32_t bits) const {
+    uint32_t m = low_mask(nbits) << (o & 31);
+    v[o >> 5] = (v[o >> 5] & ~m) | ((bits << (o & 31)) & m);
+  }
+
+  __device__ void rate0(int k, uint32_t o) const {
+    if (k >= 5) {
+      uint32_t w0 = o >> 5, nw = 1u << (k - 5);
+      for (uint32_t i = lane; i < nw; i += 32) {
+        uint32_t v = fvw[w0 + i];
+        uh[w0 + i] = v;
+        beta[w0 + i] = encode_word(v, 5);
+      }
+      xword_encode(beta, w0, nw);
+    } else {
+      if (lane == 0) {
+        uint32_t v = (fvw[o >> 5] >> (o & 31)) & low_mask(1 << k);
+        insert(uh, o, 1 << k, v);
+        insert(beta, o, 1 << k, encode_word(v, k));
+      }
+      __syncwarp();
+    }
+  }
+
+  // Rate-1 shortcut; false (nothing written) when some input is +-0.
+  __device__ bool rate1(int k, uint32_t o) const {
+    const S *Lk = lvl(k);
+    const uint32_t n = 1u << k;
+    bool z = false;
+    for (uint32_t i = lane; i < n; i += 32) z |= (Store<S>::ld(Lk + i) == 0.0f);
+    if (__any_sync(FULL, z)) return false;
+    if (k >= 5) {
+      uint32_t w0 = o >> 5, nw = 1u << (k - 5);
+      for (uint32_t i = 0; i < nw; ++i) {
+        uint32_t b = __ballot_sync(FULL, Store<S>::ld(Lk + 32 * i + lane) < 0.0f);
+        if (lane == 0) {
+          beta[w0 + i] = b;
+          uh[w0 + i] = encode_word(b, 5);
+        }
+      }
+      xword_encode(uh, w0, nw);
+    } else {
+      bool d = (uint32_t)lane < n ? (Store<S>::ld(Lk + lane) < 0.0f) : false;
+      uint32_t b = __ballot_sync(FULL, d) & low_mask(n);
+      if (lane == 0) {
+        insert(beta, o, n, b);
+        insert(uh, o, n, encode_word(b, k));
+      }
+      __syncwarp();
+    }
+    return true;
+  }
+
+  __device__ void leaf(uint32_t o) const {
+    if (lane == 0) {
+      uint32_t w = o >> 5, s = o & 31;
+      uint32_t u = ((msk[w] >> s) & 1u) ? ((fvw[w] >> s) & 1u)
+                                        : (uint32_t)(Store<S>::ld(lvl(0)) < 0.0f);
+      insert(beta, o, 1, u);
+      insert(uh, o, 1, u);
+    }
+    __syncwarp();
+  }
+
+  template <int FK>
+  __device__ void f(int k) const {
+    const S *a = lvl(k);
+    S *c = lvl(k - 1);
+    const uint32_t h = 1u << (k - 1);
+    for (uint32_t i = lane; i < h; i += 32)
+      Store<S>::st(c + i, f_op<FK>(Store<S>::ld(a + i), Store<S>::ld(a + h + i)));
+    __syncwarp();
+  }
+
+  // Right child of the node of level k whose left child starts at leaf o.
+  __device__ void g(int k, uint32_t o) const {
+    const S *a = lvl(k);
+    S *c = lvl(k - 1);
+    const uint32_t h = 1u << (k - 1);
+    for (uint32_t i = lane; i < h; i += 32) {
+      uint32_t p = o + i;
+      uint32_t u = (beta[p >> 5] >> (p & 31)) & 1u;
+      Store<S>::st(c + i, g_op(Store<S>::ld(a + i), Store<S>::ld(a + h + i), u));
+    }
+    __syncwarp();
+  }
+
+  // Parent of level K at leaf base: left half ^= right half.
+  __device__ void combine(int K, uint32_t base) const {
+    const uint32_t h = 1u << (K - 1);
+    if (h >= 32) {
+      uint32_t w0 = base >> 5, hw = h >> 5;
+      for (uint32_t i = lane; i < hw; i += 32) beta[w0 + i] ^= beta[w0 + hw + i];
+    } else if (lane == 0) {
+      uint32_t w = beta[base >> 5], s = base & 31;
+      uint32_t r = (w >> (s + h)) & low_mask(h);
+      beta[base >> 5] = w ^ (r << s);
+    }
+    __syncwarp();
+  }
+};
+
+template <typename S, int FK, bool SC>
+__global__ void __launch_bounds__(32) k_subtree(StParams p, bool in_is_llr) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int t = p.t;
+  const uint32_t T = 1u << t;
+  const uint32_t W = T >= 32 ? T / 32 : 1;
+  const int lane = threadIdx.x;
+  const size_t fr = blockIdx.x;
+
+  Warp<S> w;
+  w.lane = lane;
+  w.beta = reinterpret_cast<uint32_t *>(smraw);
+  w.uh = w.beta + W;
+  w.msk = w.beta + 2 * W;
+  w.fvw = w.beta + 3 * W;
+  w.L = reinterpret_cast<S *>(w.beta + 4 * W);
+
+  const uint64_t ow = p.o >> 5;
+  const uint32_t *fvf = p.fv + fr * p.w_stride + ow;
+  for (uint32_t i = lane; i < W; i += 32) {
+    w.msk[i] = p.mask[ow + i];
+    w.fvw[i] = fvf[i];
+    w.beta[i] = 0u;
+    w.uh[i] = 0u;
+  }
+  S *Lt = w.lvl(t);
+  if (in_is_llr) {
+    const float *src = reinterpret_cast<const float *>(p.in) + fr * p.in_stride;
+    for (uint32_t i = lane; i < T; i += 32) Store<S>::st(Lt + i, src[i]);
+  } else {
+    const S *src = reinterpret_cast<const S *>(p.in) + fr * p.in_stride;
+    for (uint32_t i = lane; i < T; i += 32) Lt[i] = src[i];
+  }
+  __syncwarp();
+
+  int k = t;
+  uint32_t o = 0;
+  for (;;) {
+    for (;;) {                                   // descend
+      if (k == 0) {
+        w.leaf(o);
+        break;
+      }
+      if (SC) {
+        int cls = w.node_class(k, o);
+        if (cls == NODE_RATE0) {
+          w.rate0(k, o);
+          break;
+        }
+        if (cls == NODE_RATE1 && w.rate1(k, o)) break;
+        if (w.node_class(k - 1, o) != NODE_RATE0) w.template f<FK>(k);
+      } else {
+        w.template f<FK>(k);
+      }
+      --k;
+    }
+    while (k < t && ((o >> k) & 1u)) {           // ascend through right children
+      w.combine(k + 1, o - (1u << k));
+      o -= 1u << k;
+      ++k;
+    }
+    if (k == t) break;
+    w.g(k + 1, o);                               // right sibling's LLRs
+    o += 1u << k;
+  }
+
+  uint32_t *xf = p.xhat + fr * p.w_stride + ow;
+  uint32_t *uf = p.uhat ? p.uhat + fr * p.w_stride + ow : nullptr;
+  const uint32_t keep = T >= 32 ? FULL : low_mask(T);
+  for (uint32_t i = lane; i < W; i += 32) {
+    xf[i] = w.beta[i] & keep;
+    if (uf) uf[i] = w.uh[i] & keep;
+  }
+  __syncthreads();
+  if (p.r > 0) cascade_device(p.xhat + fr * p.w_stride, t, p.o, p.r);
+}
+
+template <typename S, int FK, bool SC>
+cudaError_t launch_t(const SubtreeArgs &a, cudaStream_t s) {
+  const uint32_t T = 1u << a.t;
+  const uint32_t W = T >= 32 ? T / 32 : 1;
+  size_t smem = 4 * W * sizeof(uint32_t) + 2 * (size_t)T * sizeof(S);
+  auto kern = k_subtree<S, FK, SC>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  StParams p{a.in, a.in_stride, a.mask, a.fv, a.xhat, a.uhat, a.w_stride, a.o, a.t, a.r};
+  kern<<<a.nframes, 32, smem, s>>>(p, a.in_is_llr);
+  return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch_s(const SubtreeArgs &a, cudaStream_t s) {
+  if (a.fkind == 0)
+    return a.shortcuts ? launch_t<S, 0, true>(a, s) : launch_t<S, 0, false>(a, s);
+  return a.shortcuts ? launch_t<S, 1, true>(a, s) : launch_t<S, 1, false>(a, s);
+}
+
+}  // namespace
+
+cudaError_t launch_subtree(const SubtreeArgs &a, cudaStream_t s) {
+  if (a.prec == POLAR_FP16) return launch_s<__half>(a, s);
+  return launch_s<float>(a, s);
+}
+
+}  // namespace polar

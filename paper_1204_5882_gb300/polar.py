@@ -1,0 +1,200 @@
+"""Thin ctypes binding of the C ABI in ``include/polar.h``.
+
+Argument marshalling only: every function forwards to the CUDA library with
+the same name; device buffers are PyTorch tensors passed as raw pointers,
+streams as ``torch.cuda.Stream.cuda_stream``.  There is no fallback: if the
+library has not been built, importing the binding raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB_PATH
+
+POLAR_OK, POLAR_EINVAL, POLAR_ENOMEM, POLAR_ECUDA = 0, -1, -2, -3
+POLAR_ETIMEDOUT, POLAR_EBUSY, POLAR_ENOTFOUND, POLAR_PENDING = -4, -5, -6, 1
+POLAR_BSC, POLAR_BIAWGN = 0, 1
+POLAR_F_MINSUM, POLAR_F_EXACT = 0, 1
+POLAR_FP32, POLAR_FP16, POLAR_INT8 = 0, 1, 2
+
+CHANNEL = {"bsc": POLAR_BSC, "biawgn": POLAR_BIAWGN}
+FKIND = {"minsum": POLAR_F_MINSUM, "exact": POLAR_F_EXACT}
+PREC = {"fp32": POLAR_FP32, "fp16": POLAR_FP16, "int8": POLAR_INT8}
+
+
+class PolarError(RuntimeError):
+    def __init__(self, fn, status):
+        msg = f"{fn} failed: {status} ({_lib.polar_strerror(status).decode()})"
+        extra = _lib.polar_last_error_string().decode()
+        if status == POLAR_ECUDA and extra:
+            msg += f": {extra}"
+        super().__init__(msg)
+        self.status = status
+
+
+class FrameDesc(C.Structure):
+    _fields_ = [("fs", C.c_void_p), ("llr", C.c_void_p), ("frozen_vals", C.c_void_p),
+                ("xhat", C.c_void_p), ("uhat", C.c_void_p)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build the CUDA library first "
+            "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = C.CDLL(LIB_PATH)
+    P, I, U32, U64, D, SZ = C.c_void_p, C.c_int, C.c_uint32, C.c_uint64, C.c_double, C.c_size_t
+    sig = {
+        "polar_strerror": ([I], C.c_char_p),
+        "polar_last_error_string": ([], C.c_char_p),
+        "polar_config_set": ([C.c_char_p, C.c_long], I),
+        "polar_config_get": ([C.c_char_p, C.POINTER(C.c_long)], I),
+        "polar_build_frozen_set": ([U32, I, D, D, C.POINTER(P)], I),
+        "polar_frozen_set_from_mask": ([U32, P, C.POINTER(P)], I),
+        "polar_frozen_set_query": ([P, C.POINTER(U32), C.POINTER(U64), P, C.POINTER(D)], I),
+        "polar_frozen_set_free": ([P], None),
+        "polar_llr_from_channel": ([I, D, P, I, P, SZ, P], I),
+        "polar_encode": ([U32, I, P, P, P], I),
+        "polar_reveal": ([P, I, P, P, P], I),
+        "polar_sc_decode": ([P, P, P, P, P, I, I, P], I),
+        "polar_sc_decode_many": ([P, I, P, P, P, P, I, I, P], I),
+        "polar_sc_decode_batch": ([I, C.POINTER(FrameDesc), I, I, P], I),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    return L
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _check(fn, rc):
+    if rc != POLAR_OK:
+        raise PolarError(fn, rc)
+    return rc
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+# ------------------------------------------------------------------ config
+def polar_config_set(key: str, value: int):
+    _check("polar_config_set", _lib.polar_config_set(key.encode(), int(value)))
+
+
+def polar_config_get(key: str) -> int:
+    v = C.c_long()
+    _check("polar_config_get", _lib.polar_config_get(key.encode(), C.byref(v)))
+    return v.value
+
+
+# ------------------------------------------------------------------ frozen sets
+class FrozenSet:
+    """Owner of a library frozen-set object (freed on garbage collection)."""
+
+    def __init__(self, handle: int):
+        self.handle = C.c_void_p(handle)
+        n, k, s = C.c_uint32(), C.c_uint64(), C.c_double()
+        _check("polar_frozen_set_query", _lib.polar_frozen_set_query(
+            self.handle, C.byref(n), C.byref(k), None, C.byref(s)))
+        self.log2n, self.K, self.sum_pe = n.value, k.value, s.value
+        self.N = 1 << self.log2n
+        self.words = max(1, self.N // 32)
+
+    def mask(self) -> np.ndarray:
+        m = np.empty(self.words, dtype=np.uint32)
+        _check("polar_frozen_set_query", _lib.polar_frozen_set_query(
+            self.handle, None, None, m.ctypes.data_as(C.c_void_p), None))
+        return m
+
+    def __del__(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.polar_frozen_set_free(self.handle)
+            self.handle = None
+
+
+def polar_build_frozen_set(log2n: int, channel: str, param: float, rate: float) -> FrozenSet:
+    h = C.c_void_p()
+    _check("polar_build_frozen_set", _lib.polar_build_frozen_set(
+        int(log2n), CHANNEL[channel], float(param), float(rate), C.byref(h)))
+    return FrozenSet(h.value)
+
+
+def polar_frozen_set_from_mask(log2n: int, mask_words) -> FrozenSet:
+    m = np.ascontiguousarray(np.asarray(mask_words, dtype=np.uint32))
+    h = C.c_void_p()
+    _check("polar_frozen_set_from_mask", _lib.polar_frozen_set_from_mask(
+        int(log2n), m.ctypes.data_as(C.c_void_p), C.byref(h)))
+    return FrozenSet(h.value)
+
+
+# ------------------------------------------------------------------ channel / Alice
+def polar_llr_from_channel(channel: str, param: float, y, llr, stream=None):
+    import torch
+    bits = y.dtype in (torch.int32, torch.uint32)
+    _check("polar_llr_from_channel", _lib.polar_llr_from_channel(
+        CHANNEL[channel], float(param), _ptr(y), 1 if bits else 0, _ptr(llr), llr.numel(),
+        _stream(stream)))
+
+
+def polar_encode(log2n: int, nframes: int, inp, out, stream=None):
+    _check("polar_encode", _lib.polar_encode(int(log2n), int(nframes), _ptr(inp), _ptr(out),
+                                             _stream(stream)))
+
+
+def polar_reveal(fs: FrozenSet, nframes: int, x, fval, stream=None):
+    _check("polar_reveal", _lib.polar_reveal(fs.handle, int(nframes), _ptr(x), _ptr(fval),
+                                             _stream(stream)))
+
+
+# ------------------------------------------------------------------ decoding
+def polar_sc_decode(fs: FrozenSet, llr, fval, xhat, uhat=None, fkind="minsum", prec="fp32",
+                    stream=None):
+    _check("polar_sc_decode", _lib.polar_sc_decode(
+        fs.handle, _ptr(llr), _ptr(fval), _ptr(xhat), _ptr(uhat), FKIND[fkind], PREC[prec],
+        _stream(stream)))
+
+
+def polar_sc_decode_many(fs: FrozenSet, nframes: int, llr, fval, xhat, uhat=None,
+                         fkind="minsum", prec="fp32", stream=None):
+    _check("polar_sc_decode_many", _lib.polar_sc_decode_many(
+        fs.handle, int(nframes), _ptr(llr), _ptr(fval), _ptr(xhat), _ptr(uhat), FKIND[fkind],
+        PREC[prec], _stream(stream)))
+
+
+def polar_sc_decode_batch(frames, fkind="minsum", prec="fp32", stream=None):
+    """frames: list of (FrozenSet, llr, fval, xhat, uhat_or_None) tensors."""
+    arr = (FrameDesc * len(frames))()
+    for i, (fs, llr, fv, xh, uh) in enumerate(frames):
+        arr[i] = FrameDesc(fs.handle.value, llr.data_ptr(), fv.data_ptr(), xh.data_ptr(),
+                           uh.data_ptr() if uh is not None else None)
+    _check("polar_sc_decode_batch", _lib.polar_sc_decode_batch(
+        len(frames), arr, FKIND[fkind], PREC[prec], _stream(stream)))
+
+
+def exported_symbols():
+    """Names of the C ABI functions the binding declares."""
+    return [n for n in dir(_lib) if n.startswith("polar_")]

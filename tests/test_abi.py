@@ -1,0 +1,107 @@
+"""CPU checks of the C ABI: the library builds, loads, exports every function
+declared in include/*.h, and rejects bad arguments on the host before any
+CUDA call; host-side construction equals the oracle's."""
+import glob
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_1204_5882_gb300 import build
+    build.build()
+    from paper_1204_5882_gb300 import polar
+    return polar
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(polar_\w+)\s*\(", src))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(P):
+    names = declared_functions()
+    assert len(names) >= 14
+    out = subprocess.run(["nm", "-D", "--defined-only", P.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (polar_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        assert hasattr(P.lib(), n)
+
+
+def test_library_is_built_for_sm_103a(P):
+    log = open(os.path.join(os.path.dirname(P.LIB_PATH), "subtree.cu.log")).read()
+    assert "arch=compute_103a,code=sm_103a" in log
+
+
+def test_strerror_and_config(P):
+    assert P.lib().polar_strerror(-1).decode() == "invalid argument"
+    old = P.polar_config_get("subtree_log2")
+    P.polar_config_set("subtree_log2", 9)
+    assert P.polar_config_get("subtree_log2") == 9
+    P.polar_config_set("subtree_log2", old)
+    with pytest.raises(P.PolarError):
+        P.polar_config_set("subtree_log2", 40)
+    with pytest.raises(P.PolarError):
+        P.polar_config_set("no_such_key", 1)
+
+
+def test_argument_errors_are_host_side(P):
+    L = P.lib()
+    fs = P.polar_build_frozen_set(10, "bsc", 0.03, 0.5)
+    # null device pointers / bad enums / bad counts: rejected before any CUDA call
+    assert L.polar_sc_decode_many(fs.handle, 1, None, None, None, None, 0, 0, None) == P.POLAR_EINVAL
+    assert L.polar_sc_decode_many(fs.handle, 0, 16, 16, 16, None, 0, 0, None) == P.POLAR_EINVAL
+    assert L.polar_sc_decode_many(fs.handle, 1, 16, 16, 16, None, 7, 0, None) == P.POLAR_EINVAL
+    assert L.polar_sc_decode_many(fs.handle, 1, 16, 16, 16, None, 0, 9, None) == P.POLAR_EINVAL
+    assert L.polar_sc_decode_many(fs.handle, 1, 18, 16, 16, None, 0, 0, None) == P.POLAR_EINVAL
+    assert L.polar_sc_decode_many(None, 1, 16, 16, 16, None, 0, 0, None) == P.POLAR_EINVAL
+    assert L.polar_llr_from_channel(0, 0.7, 16, 1, 16, 64, None) == P.POLAR_EINVAL
+    assert L.polar_llr_from_channel(0, 0.1, 16, 0, 16, 64, None) == P.POLAR_EINVAL
+    assert L.polar_llr_from_channel(0, 0.1, 16, 1, 16, 33, None) == P.POLAR_EINVAL
+    assert L.polar_llr_from_channel(1, -1.0, 16, 0, 16, 64, None) == P.POLAR_EINVAL
+    assert L.polar_llr_from_channel(1, 1.0, 16, 0, 16, 0, None) == P.POLAR_OK   # empty
+    assert L.polar_encode(0, 1, 16, 16, None) == P.POLAR_EINVAL
+    assert L.polar_encode(27, 1, 16, 16, None) == P.POLAR_EINVAL
+    with pytest.raises(P.PolarError):
+        P.polar_build_frozen_set(10, "bsc", 0.7, 0.5)
+    with pytest.raises(P.PolarError):
+        P.polar_build_frozen_set(0, "bsc", 0.1, 0.5)
+    with pytest.raises(P.PolarError):
+        P.polar_build_frozen_set(10, "biawgn", 1.0, 1.5)
+
+
+@pytest.mark.parametrize("case", [(10, "bsc", 0.02, 0.8), (16, "bsc", 0.02, 0.80),
+                                  (20, "bsc", 0.03, 0.75), (12, "biawgn", 1.0, 0.44),
+                                  (18, "biawgn", 1.0, 0.44), (14, "biawgn", 0.5, 0.93),
+                                  (1, "bsc", 0.1, 0.5), (4, "biawgn", 2.0, 0.25)])
+def test_library_construction_equals_oracle(P, case):
+    import oracle as O
+    from paper_1204_5882_gb300 import synth as S
+    n, ch, par, R = case
+    fs = P.polar_build_frozen_set(n, ch, par, R)
+    ofz, K = O.frozen_set(n, ch, par, R)
+    assert fs.K == K
+    assert np.array_equal(S.unpack_bits(fs.mask(), 1 << n), ofz)
+    assert fs.sum_pe == pytest.approx(O.fer_bound(n, ch, par, ofz), rel=1e-9)
+
+
+def test_frozen_set_from_mask_roundtrip(P):
+    m = np.array([0xDEADBEEF, 0x0], dtype=np.uint32)
+    fs = P.polar_frozen_set_from_mask(6, m)
+    assert np.array_equal(fs.mask(), m)
+    assert fs.K == 64 - bin(0xDEADBEEF).count("1")
+    fs = P.polar_frozen_set_from_mask(3, np.array([0xFFFFFF0F], dtype=np.uint32))
+    assert fs.mask()[0] == 0x0F and fs.K == 4

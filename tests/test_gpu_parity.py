@@ -1,0 +1,246 @@
+"""GPU parity of the CUDA path against the CPU oracle, through the C ABI.
+
+Bar: bit-exact x_hat and u_hat for float32 min-sum SC (every frame compared
+element by element); bit-exact LLR maps, transforms and reveals; exact-f
+frame error rate within two binomial standard errors of the float64 oracle.
+Inputs come from the seeded generators in paper_1204_5882_gb300.synth; each
+side builds its own frozen set and they are asserted equal first.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle as O  # noqa: E402
+from paper_1204_5882_gb300 import synth as S  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1204_5882_gb300 import build
+    build.build()
+    from paper_1204_5882_gb300 import polar
+    return polar
+
+
+DEV = "cuda:0"
+
+
+def to_dev_words(a):
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(DEV)
+
+
+def words_np(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+@pytest.fixture(autouse=True)
+def default_config(P):
+    saved = {k: P.polar_config_get(k) for k in ("subtree_log2", "shortcuts", "graphs", "plain")}
+    yield
+    for k, v in saved.items():
+        P.polar_config_set(k, v)
+
+
+def gpu_decode(P, fs, llr_np, fv_words, fkind="minsum", prec="fp32", uhat=True):
+    F = llr_np.shape[0]
+    llr = torch.from_numpy(np.ascontiguousarray(llr_np, dtype=np.float32)).to(DEV)
+    fv = to_dev_words(fv_words)
+    xh = torch.full_like(fv, -1)
+    uh = torch.full_like(fv, -1) if uhat else None
+    P.polar_sc_decode_many(fs, F, llr, fv, xh, uh, fkind, prec)
+    torch.cuda.synchronize()
+    return words_np(xh), (words_np(uh) if uhat else None)
+
+
+# ------------------------------------------------------------------ maps
+def test_llr_bsc_bitexact(P):
+    w = S.WORKLOADS["bsc_p02_n16"]
+    x, y = S.frames(w, 0, 3)
+    llr = torch.empty(3, w.N, dtype=torch.float32, device=DEV)
+    P.polar_llr_from_channel("bsc", w.param, to_dev_words(y), llr)
+    got = llr.cpu().numpy()
+    for f in range(3):
+        assert np.array_equal(got[f], O.llr_bsc(S.unpack_bits(y[f], w.N), w.param, 32))
+
+
+@pytest.mark.parametrize("count", [2 ** 16, 2 ** 16 + 1, 7])
+def test_llr_biawgn_bitexact(P, count):
+    rng = np.random.default_rng(3)
+    y = rng.normal(1.0, 1.0, count)
+    yd = torch.from_numpy(y).to(DEV)
+    llr = torch.empty(count, dtype=torch.float32, device=DEV)
+    P.polar_llr_from_channel("biawgn", 0.7, yd, llr)
+    assert np.array_equal(llr.cpu().numpy(), O.llr_biawgn(y, 0.7, 32))
+
+
+@pytest.mark.parametrize("n", [1, 3, 5, 6, 10, 17, 18, 22])
+def test_encode_matches_oracle(P, n):
+    N = 1 << n
+    F = 3
+    rng = np.random.default_rng(n)
+    u = rng.integers(0, 2, (F, N)).astype(np.uint8)
+    words = np.stack([S.pack_bits(r) for r in u])
+    ud = to_dev_words(words)
+    out = torch.zeros_like(ud)
+    P.polar_encode(n, F, ud, out)
+    got = words_np(out)
+    for f in range(F):
+        assert np.array_equal(S.unpack_bits(got[f], N), O.encode(u[f]))
+    P.polar_encode(n, F, ud, ud)           # in place
+    assert np.array_equal(words_np(ud), got)
+
+
+def test_reveal_matches_oracle(P):
+    n, F = 16, 4
+    fs = P.polar_build_frozen_set(n, "bsc", 0.02, 0.8)
+    ofz, _ = O.frozen_set(n, "bsc", 0.02, 0.8)
+    x, _ = S.frames(S.WORKLOADS["bsc_p02_n16"], 0, F)
+    fv = torch.zeros(F, (1 << n) // 32, dtype=torch.int32, device=DEV)
+    P.polar_reveal(fs, F, to_dev_words(x), fv)
+    got = words_np(fv)
+    for f in range(F):
+        assert np.array_equal(S.unpack_bits(got[f], 1 << n), O.reveal(S.unpack_bits(x[f], 1 << n), ofz))
+
+
+# ------------------------------------------------------------------ min-sum bit-exact
+def random_code(rng, n, kind):
+    N = 1 << n
+    if kind == "random":
+        fz = (rng.random(N) < 0.5).astype(np.uint8)
+    elif kind == "all_frozen":
+        fz = np.ones(N, np.uint8)
+    elif kind == "all_info":
+        fz = np.zeros(N, np.uint8)
+    else:   # polar-like: Bhattacharyya set of a BSC
+        fz, _ = O.frozen_set(n, "bsc", 0.05, 0.6)
+    return fz
+
+
+def check_minsum(P, n, kind, F, seed, llr_kind="gauss"):
+    N = 1 << n
+    rng = np.random.default_rng(seed)
+    fz = random_code(rng, n, kind)
+    fs = P.polar_frozen_set_from_mask(n, S.pack_bits(fz))
+    if llr_kind == "gauss":
+        L = rng.normal(0.5, 2.0, (F, N)).astype(np.float32)
+    else:   # BSC-like: +-c with many exact ties in g
+        L = (np.float32(2.5) * (1 - 2 * (rng.random((F, N)) < 0.1))).astype(np.float32)
+    fvb = (rng.integers(0, 2, (F, N)) * fz).astype(np.uint8)
+    fvw = np.stack([S.pack_bits(r) for r in fvb])
+    xh, uh = gpu_decode(P, fs, L, fvw)
+    for f in range(F):
+        ou, ox = O.sc_decode(L[f], fz, fvb[f], "minsum")
+        assert np.array_equal(S.unpack_bits(xh[f], N), ox), (n, kind, f)
+        assert np.array_equal(S.unpack_bits(uh[f], N), ou), (n, kind, f)
+
+
+@pytest.mark.parametrize("t", [5, 8, 13])
+@pytest.mark.parametrize("n", [1, 2, 4, 5, 6, 9, 12, 15])
+@pytest.mark.parametrize("kind", ["random", "polar", "all_info", "all_frozen"])
+def test_minsum_bitexact_small(P, n, kind, t):
+    P.polar_config_set("subtree_log2", t)
+    check_minsum(P, n, kind, F=3, seed=1000 * n + t, llr_kind="gauss")
+    check_minsum(P, n, kind, F=2, seed=1000 * n + t + 7, llr_kind="bsc")
+
+
+@pytest.mark.parametrize("mode", ["no_shortcuts", "no_graphs", "plain"])
+def test_minsum_bitexact_modes(P, mode):
+    if mode == "no_shortcuts":
+        P.polar_config_set("shortcuts", 0)
+    elif mode == "no_graphs":
+        P.polar_config_set("graphs", 0)
+    else:
+        P.polar_config_set("plain", 1)
+    P.polar_config_set("subtree_log2", 9)
+    for n, kind in ((12, "polar"), (14, "random"), (11, "all_info")):
+        check_minsum(P, n, kind, F=3, seed=77 + n, llr_kind="bsc")
+
+
+def test_batch_of_mixed_frames(P):
+    """polar_sc_decode_batch with frames of several lengths and codes."""
+    rng = np.random.default_rng(5)
+    frames, expect = [], []
+    for n in (10, 12, 12, 16, 10):
+        N = 1 << n
+        fz = random_code(rng, n, "polar")
+        fs = P.polar_frozen_set_from_mask(n, S.pack_bits(fz))
+        L = rng.normal(0.5, 2.0, N).astype(np.float32)
+        fvb = (rng.integers(0, 2, N) * fz).astype(np.uint8)
+        llr = torch.from_numpy(L).to(DEV)
+        fv = to_dev_words(S.pack_bits(fvb))
+        xh = torch.zeros_like(fv)
+        frames.append((fs, llr, fv, xh, None))
+        expect.append(O.sc_decode(L, fz, fvb, "minsum")[1])
+    P.polar_sc_decode_batch(frames)
+    torch.cuda.synchronize()
+    for (fs, _, _, xh, _), ox in zip(frames, expect):
+        assert np.array_equal(S.unpack_bits(words_np(xh), fs.N), ox)
+
+
+def decode_workload_gpu(P, w, first, count, fkind="minsum", prec="fp32"):
+    fs = P.polar_build_frozen_set(w.log2n, w.channel, w.param, w.rate)
+    x, y = S.frames(w, first, count)
+    xd = to_dev_words(x)
+    fv = torch.empty_like(xd)
+    P.polar_reveal(fs, count, xd, fv)
+    llr = torch.empty(count, w.N, dtype=torch.float32, device=DEV)
+    if w.channel == "bsc":
+        P.polar_llr_from_channel("bsc", w.param, to_dev_words(y), llr)
+    else:
+        P.polar_llr_from_channel("biawgn", w.param, torch.from_numpy(y).to(DEV), llr)
+    xh = torch.zeros_like(xd)
+    uh = torch.zeros_like(xd)
+    P.polar_sc_decode_many(fs, count, llr, fv, xh, uh, fkind, prec)
+    torch.cuda.synchronize()
+    return fs, x, y, words_np(xh), words_np(uh)
+
+
+@pytest.mark.parametrize("name,check", [("bsc_p02_n16", 100), ("bsc_p03_n20", 16)])
+def test_workload_minsum_bitexact(P, name, check):
+    w = S.WORKLOADS[name]
+    fs, x, y, xh, uh = decode_workload_gpu(P, w, 0, w.frames)
+    ofz, _ = O.frozen_set(w.log2n, w.channel, w.param, w.rate)
+    assert np.array_equal(S.unpack_bits(fs.mask(), w.N), ofz)
+    for f in range(check):
+        ou, ox, _ = O.decode_frame(w.channel, w.param, x[f], y[f], ofz, "minsum", 32)
+        assert np.array_equal(S.unpack_bits(xh[f], w.N), ox), f
+        assert np.array_equal(S.unpack_bits(uh[f], w.N), ou), f
+
+
+def test_workload_biawgn_2_24_sampled(P):
+    """Full-size BI-AWGN workload (16 frames of 2^24) decoded together; four
+    frames compared element by element with the float32 min-sum oracle."""
+    w = S.WORKLOADS["biawgn_s1_n24"]
+    fs, x, y, xh, uh = decode_workload_gpu(P, w, 0, w.frames)
+    ofz, _ = O.frozen_set(w.log2n, w.channel, w.param, w.rate)
+    assert np.array_equal(S.unpack_bits(fs.mask(), w.N), ofz)
+    for f in (0, 5, 10, 15):
+        ou, ox, _ = O.decode_frame(w.channel, w.param, x[f], y[f], ofz, "minsum", 32)
+        assert np.array_equal(S.unpack_bits(xh[f], w.N), ox), f
+
+
+# ------------------------------------------------------------------ exact f, statistics
+def test_exact_f_fer_matches_float64_oracle(P):
+    """Exact-f FP32 on the GPU vs exact-f FP64 oracle on the same frames:
+    FERs within two binomial standard errors (BI-AWGN sigma^2 = 1, N = 2^12,
+    rate chosen so that the FER sits mid-range)."""
+    w = S.Workload("fer_biawgn_n12", "biawgn", 1.0, 12, 0.40, 400, 0x5EED + 40)
+    fs, x, y, xh, _ = decode_workload_gpu(P, w, 0, w.frames, fkind="exact")
+    ofz, _ = O.frozen_set(w.log2n, w.channel, w.param, w.rate)
+    g_err = o_err = 0
+    for f in range(w.frames):
+        xb = S.unpack_bits(x[f], w.N)
+        g_err += int(not np.array_equal(S.unpack_bits(xh[f], w.N), xb))
+        _, ox, _ = O.decode_frame(w.channel, w.param, x[f], y[f], ofz, "exact", 64)
+        o_err += int(not np.array_equal(ox, xb))
+    T = w.frames
+    pg, po = g_err / T, o_err / T
+    se = math.sqrt(max(pg * (1 - pg), 1.0 / T) / T + max(po * (1 - po), 1.0 / T) / T)
+    assert 0.02 < po < 0.98, po
+    assert abs(pg - po) <= 2 * se, (pg, po, se)
