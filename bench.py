@@ -1,0 +1,433 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of GB300 SC polar decoding (syndrome-form QKD error
+correction, Jouguet & Kunz-Jacques, arXiv 1204.5882, Table 1's workloads).
+
+One step = the whole hot path over one batch: channel LLR map + SC decode of
+every frame of the batch (default: 64 frames of N = 2^20, BSC p = 0.03,
+rate 0.75, float32 min-sum).  Metric: decoded Mbit/s = N * frames / time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                  [--impl ours|reference]
+
+Under torchrun every rank decodes its own frames (frames are independent:
+replicas, weak scaling, no collective on the data path); time = max over
+ranks.  ``--impl reference`` times the plain CPU oracle on the host cores
+(rank 0 only) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1204_5882_gb300 import synth as S  # noqa: E402
+
+METRIC = "decoded Mbit/s"
+UNIT = "Mbit/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="bsc_p03_n20", choices=sorted(S.WORKLOADS))
+    ap.add_argument("--fkind", default="minsum", choices=["minsum", "exact"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp16"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain per-frame baseline")
+    return ap.parse_args()
+
+
+def config_of(w, args, extra=None):
+    c = {"workload": w.name, "N": w.N, "log2n": w.log2n, "frames_per_gpu": w.frames,
+         "channel": w.channel, "param": w.param, "rate": w.rate, "K": w.K,
+         "fkind": args.fkind, "storage": args.prec, "parallelism": "replicas",
+         "l2": "flushed (256 MB write) between timed steps; LLR arrays exceed L2"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ------------------------------------------------------------------ CPU oracle
+_W = {}
+
+
+def _oracle_init(name, mask_bytes):
+    import oracle as O
+    O.lib()
+    _W["w"] = S.WORKLOADS[name]
+    _W["fz"] = np.frombuffer(mask_bytes, dtype=np.uint8)
+
+
+def _oracle_frame(f):
+    """Bob's side of one frame on the oracle: LLR map + float32 min-sum SC,
+    timed; input generation and Alice's reveal are not."""
+    import oracle as O
+    w, fz = _W["w"], _W["fz"]
+    x, y = S.frame(w, f)
+    fv = O.reveal(O.unpack(x, w.N), fz)
+    yb = O.unpack(y, w.N) if w.channel == "bsc" else y
+    t0 = time.perf_counter()
+    L = O.llr_bsc(yb, w.param, 32) if w.channel == "bsc" else O.llr_biawgn(yb, w.param, 32)
+    O.sc_decode(L, fz, fv, "minsum")
+    return time.perf_counter() - t0
+
+
+def oracle_pool(w):
+    """Spawned worker pool over the host cores, with the oracle's frozen set."""
+    import oracle as O
+    O.build()
+    fz, _ = O.frozen_set(w.log2n, w.channel, w.param, w.rate)
+    cores = min(os.cpu_count() or 1, 64)
+    ctx = mp.get_context("spawn")
+    pool = ctx.Pool(cores, initializer=_oracle_init, initargs=(w.name, fz.tobytes()))
+    pool.map(_oracle_frame, [0] * cores)          # warm: imports, page-in
+    return pool, cores
+
+
+def oracle_step(pool, w, first, count):
+    """Decode frames first..first+count-1 on the pool; per-frame decode seconds
+    (input generation excluded)."""
+    return pool.map(_oracle_frame, range(first, first + count), chunksize=1)
+
+
+def oracle_rate(times, cores, N):
+    """Aggregate rate of `cores` independent workers at the measured per-frame
+    speed, in Mbit/s."""
+    return cores * N / statistics.mean(times) / 1e6
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = S.WORKLOADS[args.workload]
+    pool, cores = oracle_pool(w)
+    sample = cores if w.log2n >= 22 else 2 * cores
+    rates, step_s = [], []
+    for i in range(args.warmup + args.steps):
+        times = oracle_step(pool, w, i * sample, sample)
+        if i >= args.warmup:
+            rates.append(oracle_rate(times, cores, w.N))
+            step_s.append(sum(times) / cores)
+    pool.close()
+    value = statistics.mean(rates)
+    mean = statistics.mean(step_s)
+    cpu = {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{sample} frames of {w.name} per step (float32 min-sum recursive SC, "
+                     f"LLR map included), one frame per process at a time; rate = processes x "
+                     f"N / mean per-frame time"}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": mean * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_of(w, args, {"frames_per_step": sample}), "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.idx is not None:
+            cmd[1:1] = ["-i", str(self.idx)]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for ln in open(self.path):
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+# ------------------------------------------------------------------ ours
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1204_5882_gb300 import polar as P
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    w = S.WORKLOADS[args.workload]
+    F, N = w.frames, w.N
+    first = rank * F
+
+    # CPU baseline pool first (spawned, before heavy GPU work).
+    pool = cores = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        pool, cores = oracle_pool(w)
+
+    fs = P.polar_build_frozen_set(w.log2n, w.channel, w.param, w.rate)
+    x, y = S.frames(w, first, F)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        xd = torch.from_numpy(x.view(np.int32)).to(dev)
+        if w.channel == "bsc":
+            yd = torch.from_numpy(y.view(np.int32)).to(dev)
+        else:
+            yd = torch.from_numpy(y).to(dev)
+        fv = torch.empty_like(xd)
+        P.polar_reveal(fs, F, xd, fv, stream)
+        llr = torch.empty(F, N, dtype=torch.float32, device=dev)
+        xh = torch.empty_like(xd)
+        flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+        def step(yy=yd, ff=fv, out=xh):
+            P.polar_llr_from_channel(w.channel, w.param, yy, llr, stream)
+            P.polar_sc_decode_many(fs, F, llr, ff, out, None, args.fkind, args.prec, stream)
+
+        for _ in range(args.warmup):
+            step()
+        stream.synchronize()
+        fer = float((xh != xd).any(dim=1).float().mean().item())
+
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        gpu_idx = None
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        if vis:
+            ids = vis.split(",")
+            gpu_idx = ids[local] if local < len(ids) and ids[local].isdigit() else None
+        else:
+            gpu_idx = local
+        clocks = ClockSampler(gpu_idx)
+        clocks.start()
+        launches0 = P.polar_kernel_launches()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        stream.synchronize()
+        launches = P.polar_kernel_launches() - launches0
+        ck = clocks.stop()
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        total_ms = sum(step_ms)
+        if world > 1:
+            t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        ms_step = total_ms / args.steps
+        value = world * F * N / (ms_step / 1e3) / 1e6
+
+        # ---- end to end through the public API with pinned host buffers
+        if w.channel == "bsc":
+            y_host = torch.from_numpy(y.view(np.int32)).pin_memory()
+        else:
+            y_host = torch.from_numpy(y).pin_memory()
+        fv_host = fv.cpu().pin_memory()
+        xh_host = torch.empty(xh.shape, dtype=xh.dtype).pin_memory()
+        yd2, fv2, xh2 = torch.empty_like(yd), torch.empty_like(fv), torch.empty_like(xh)
+        e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+
+        def e2e_step():
+            yd2.copy_(y_host, non_blocking=True)
+            fv2.copy_(fv_host, non_blocking=True)
+            step(yd2, fv2, xh2)
+            xh_host.copy_(xh2, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        stream.synchronize()
+        for i in range(args.steps):
+            flush.zero_()
+            e2e_ev[i][0].record(stream)
+            e2e_step()
+            e2e_ev[i][1].record(stream)
+        stream.synchronize()
+        e2e_ms = [a.elapsed_time(b) for a, b in e2e_ev]
+        assert torch.equal(xh_host, xh.cpu()), "end-to-end output differs from the resident run"
+        e2e_ms_mean = sum(e2e_ms) / len(e2e_ms)
+        if world > 1:
+            t = torch.tensor([e2e_ms_mean], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms_mean = float(t.item())
+        e2e = {"value": world * F * N / (e2e_ms_mean / 1e3) / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(y_host.numel() * y_host.element_size()
+                                         + fv_host.numel() * fv_host.element_size()),
+               "d2h_bytes_per_step": int(xh_host.numel() * xh_host.element_size()),
+               "ms_per_step": e2e_ms_mean}
+
+        # ---- per-kernel timing pass (eager launches, CUDA events on the stream)
+        P.polar_config_set("profile", 1)
+        P.polar_profile_reset()
+        flush.zero_()
+        step()
+        stream.synchronize()
+        prof = {k: P.polar_profile_read(k) for k in P.PROFILE_KINDS}
+        P.polar_config_set("profile", 0)
+
+        # ---- plain per-frame baseline on a few frames
+        plain = None
+        if not args.no_plain:
+            nplain = min(F, 2 if N >= (1 << 20) else 8)
+            P.polar_config_set("plain", 1)
+            P.polar_sc_decode_many(fs, nplain, llr, fv, xh, None, args.fkind, "fp32", stream)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.zero_()
+            a.record(stream)
+            P.polar_llr_from_channel(w.channel, w.param, yd[:nplain], llr[:nplain], stream)
+            P.polar_sc_decode_many(fs, nplain, llr, fv, xh, None, args.fkind, "fp32", stream)
+            b.record(stream)
+            stream.synchronize()
+            P.polar_config_set("plain", 0)
+            pms = a.elapsed_time(b)
+            plain = {"value": nplain * N / (pms / 1e3) / 1e6, "unit": UNIT,
+                     "frames_timed": nplain, "ms": pms,
+                     "what": "one frame after another, float32 min-sum, no shortcuts, "
+                             "no graphs, eager launches"}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel and of the streamed stages
+    peaks = measured_peaks()
+    hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s"
+    dom = max(prof, key=lambda k: prof[k][0])
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    clock_ghz = (ck.get("sm_max_mhz") or 2070.0) / 1e3
+
+    def hbm_roof(kinds):
+        ms = sum(prof[k][0] for k in kinds)
+        by = sum(prof[k][2] for k in kinds)
+        n = sum(prof[k][1] for k in kinds)
+        if ms <= 0 or n == 0:
+            return None
+        ach = by / (ms / 1e3) / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": None, "peak_source": peak_src,
+                "kernels": list(kinds), "launches": n, "avg_launch_us": ms / n * 1e3,
+                "alg_bytes_per_launch": by / n}
+
+    if dom == "subtree":
+        ms, n, _ = prof["subtree"]
+        t = min(w.log2n, P.polar_config_get("subtree_log2"))
+        ops = n * F * t * (1 << t)                  # f/g evaluations of the recursion
+        ach = ops / (ms / 1e3) / 1e12
+        alu_peak = sm_count * 128 * clock_ghz / 1e3  # T simple FP32 ops/s
+        roof = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "Tops/s",
+                "frac": ach / alu_peak, "traffic": None, "kernel": "subtree",
+                "launches": n, "avg_launch_us": ms / n * 1e3,
+                "work_per_launch": f"{F} frames x t*2^t = {F * t * (1 << t)} f/g evaluations",
+                "peak_source": f"{sm_count} SMs x 128 FP32 lanes x {clock_ghz:.2f} GHz",
+                "ns_per_leaf_per_frame": ms * 1e6 / (n * (1 << t))}
+    else:
+        roof = hbm_roof([dom])
+    kernel_share = {k: {"ms": prof[k][0], "launches": prof[k][1]} for k in prof}
+
+    cpu = None
+    if pool is not None:
+        sample = cores
+        times = oracle_step(pool, w, 0, sample)
+        pool.close()
+        cpu = {"value": oracle_rate(times, cores, N), "unit": UNIT, "cores": cores,
+               "kind": "oracle", "single_core": N / statistics.mean(times) / 1e6,
+               "sample": f"{sample} frames of {w.name} (float32 min-sum recursive SC with the "
+                         f"LLR map), one frame per process; rate = processes x N / mean "
+                         f"per-frame time"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.prec == "fp32" else "f32 compute, f16 storage",
+            "data": "synthetic", "config": config_of(w, args),
+            "roofline": roof, "roofline_streamed": hbm_roof(["stream_f", "stream_g"]),
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": ck, "plain_sc": plain, "fer": fer,
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                           "p99": float(np.percentile(step_ms, 99)),
+                           "what": "batch frames all complete at the end of their step"},
+            "kernel_time_ms": kernel_share}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

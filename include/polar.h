@@ -76,9 +76,27 @@ const char *polar_last_error_string(void);
  *                   (default), 0 = launch every kernel eagerly.
  *   "plain"         1 = the plain per-frame baseline: frames decoded one
  *                   after another, no shortcuts, no graphs; 0 (default).
+ *   "profile"       1 = time every kernel group with CUDA events (eager
+ *                   launches, see polar_profile_read); 0 (default).
  */
 int polar_config_set(const char *key, long value);
 int polar_config_get(const char *key, long *value);
+
+/* Cumulative number of kernels this library has launched in this process,
+ * kernels inside replayed CUDA graphs included. */
+uint64_t polar_kernel_launches(void);
+
+/* Per-kind kernel timing, for profiling.  While the "profile" option is 1,
+ * decode and map calls launch eagerly (no graphs) and bracket every kernel
+ * group with CUDA events on the launching stream.  polar_profile_read
+ * synchronises the recorded events and returns, for one kind ("llr",
+ * "stream_f", "stream_g", "subtree", "rate0"), the summed device time in ms,
+ * the number of launches and the algorithmic bytes those launches move
+ * (inputs read once, outputs written once).  polar_profile_reset discards
+ * what was recorded.  Any pointer may be NULL. */
+int polar_profile_read(const char *kind, double *total_ms, uint64_t *launches,
+                       double *alg_bytes);
+void polar_profile_reset(void);
 
 /* --------------------------------------------------------- construction */
 

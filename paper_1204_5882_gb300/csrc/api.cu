@@ -20,8 +20,60 @@ struct Config {
   std::atomic<long> shortcuts{1};
   std::atomic<long> graphs{1};
   std::atomic<long> plain{0};
+  std::atomic<long> profile{0};
 };
 Config g_cfg;
+
+// ---------------------------------------------------------------- profiling
+struct ProfRec {
+  int kind;
+  cudaEvent_t a, b;
+  double bytes;
+};
+const char *const kKinds[] = {"llr", "stream_f", "stream_g", "subtree", "rate0"};
+constexpr int kNumKinds = 5;
+std::mutex g_prof_mu;
+std::vector<ProfRec> g_prof_pending;
+double g_prof_ms[kNumKinds];
+uint64_t g_prof_n[kNumKinds];
+double g_prof_bytes[kNumKinds];
+
+struct ProfScope {
+  bool on;
+  int kind;
+  double bytes;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(bool enable, int k, double by, cudaStream_t st) : on(enable), kind(k), bytes(by), s(st) {
+    if (!on) return;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+      on = false;
+      return;
+    }
+    cudaEventRecord(a, s);
+  }
+  ~ProfScope() {
+    if (!on) return;
+    cudaEventRecord(b, s);
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    g_prof_pending.push_back({kind, a, b, bytes});
+  }
+};
+
+void prof_drain() {
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  for (auto &r : g_prof_pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      g_prof_ms[r.kind] += ms;
+      g_prof_n[r.kind] += 1;
+      g_prof_bytes[r.kind] += r.bytes;
+    }
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  g_prof_pending.clear();
+}
 
 int cuda_fail(cudaError_t e) {
   g_last_error = cudaGetErrorString(e);
@@ -76,8 +128,12 @@ int get_workspace(int dev, cudaStream_t s, size_t bytes, void **out) {
 // ---------------------------------------------------------------- graphs
 using GraphKey = std::tuple<uint64_t, int, const void *, const void *, const void *, const void *,
                             int, int, int, int, cudaStream_t, int, const void *>;
+struct GraphEntry {
+  cudaGraphExec_t exec;
+  uint64_t kernels;
+};
 std::mutex g_graph_mu;
-std::list<std::pair<GraphKey, cudaGraphExec_t>> g_graphs;   // most recent first
+std::list<std::pair<GraphKey, GraphEntry>> g_graphs;   // most recent first
 constexpr size_t kMaxGraphs = 32;
 
 // ---------------------------------------------------------------- decoding
@@ -105,11 +161,12 @@ inline void *level_ptr(const Exec &x, int k) {
   return static_cast<char *>(x.ws) + off * storage_bytes(x.g->prec);
 }
 
-int run_ops(const Exec &x, cudaStream_t s) {
+int run_ops(const Exec &x, cudaStream_t s, bool prof) {
   const Group &g = *x.g;
   const int n = x.n, t = x.t;
   const uint64_t N = uint64_t(1) << n;
   const size_t W = N >= 32 ? N / 32 : 1;
+  const double F = g.nframes, sb = (double)storage_bytes(g.prec);
   for (const Op &op : x.plan->ops) {
     switch (op.kind) {
       case OP_F:
@@ -120,6 +177,9 @@ int run_ops(const Exec &x, cudaStream_t s) {
         const size_t ins = top ? N : (size_t(1) << k);
         void *out = level_ptr(x, k - 1);
         const uint64_t h = uint64_t(1) << (k - 1);
+        const double inb = top ? 4.0 : sb;
+        ProfScope ps(prof, op.kind == OP_F ? 1 : 2,
+                     F * (2.0 * h * inb + h * sb + (op.kind == OP_G ? h / 8.0 : 0.0)), s);
         if (op.kind == OP_F) {
           CK(launch_stream_f(g.prec, g.fkind, in, ins, top, out, h, h, g.nframes, s));
         } else {
@@ -144,11 +204,19 @@ int run_ops(const Exec &x, cudaStream_t s) {
         a.fkind = g.fkind;
         a.prec = g.prec;
         a.shortcuts = x.plan->shortcuts;
+        const double T = double(uint64_t(1) << t);
+        double cb = 0;
+        for (int m = 0; m < op.r; ++m) cb += 3.0 * double(uint64_t(1) << (t + m)) / 8.0;
+        ProfScope ps(prof, 3,
+                     F * (T * (a.in_is_llr ? 4.0 : sb) + T / 8.0 * (g.uhat ? 4 : 3) + cb), s);
         CK(launch_subtree(a, s));
         break;
       }
       case OP_R0: {
         const size_t off = op.o >> 5, nw = size_t(1) << (op.k - 5);
+        double cb = 0;
+        for (int m = 0; m < op.r; ++m) cb += 3.0 * double(uint64_t(1) << (op.k + m)) / 8.0;
+        ProfScope ps(prof, 4, F * (nw * 4.0 * (g.uhat ? 3 : 2) + cb), s);
         CK(launch_copy_regions(g.fv, g.xhat, W, off, nw, g.nframes, nullptr, s));
         if (g.uhat) CK(launch_copy_regions(g.fv, g.uhat, W, off, nw, g.nframes, nullptr, s));
         CK(launch_encode_regions(g.xhat, W, off, op.k, g.nframes, s));
@@ -199,28 +267,31 @@ int decode_group(const Group &g, cudaStream_t s) {
       one.xhat = g.xhat + (size_t)f * W;
       one.uhat = g.uhat ? g.uhat + (size_t)f * W : nullptr;
       Exec x{plan.get(), &one, dmask, ws, n, t};
-      rc = run_ops(x, s);
+      rc = run_ops(x, s, g_cfg.profile.load() != 0);
       if (rc) return rc;
     }
     return POLAR_OK;
   }
   Exec x{plan.get(), &g, dmask, ws, n, t};
-  bool use_graph = graphs && s != nullptr;
+  const bool prof = g_cfg.profile.load() != 0;
+  bool use_graph = graphs && !prof && s != nullptr;
   if (use_graph) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     CK(cudaStreamIsCapturing(s, &cs));
     if (cs != cudaStreamCaptureStatusNone) use_graph = false;   // caller is capturing
   }
-  if (!use_graph) return run_ops(x, s);
+  if (!use_graph) return run_ops(x, s, prof);
 
   GraphKey key{fs->id, g.nframes, g.llr, g.fv, g.xhat, g.uhat, g.fkind, g.prec, t,
                shortcuts ? 1 : 0, s, dev, ws};
   cudaGraphExec_t exec = nullptr;
+  uint64_t kernels = 0;
   {
     std::lock_guard<std::mutex> lk(g_graph_mu);
     for (auto it = g_graphs.begin(); it != g_graphs.end(); ++it) {
       if (it->first == key) {
-        exec = it->second;
+        exec = it->second.exec;
+        kernels = it->second.kernels;
         g_graphs.splice(g_graphs.begin(), g_graphs, it);
         break;
       }
@@ -228,7 +299,10 @@ int decode_group(const Group &g, cudaStream_t s) {
   }
   if (!exec) {
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
-    rc = run_ops(x, s);
+    const uint64_t before = g_kernel_launches.load();
+    rc = run_ops(x, s, false);
+    kernels = g_kernel_launches.load() - before;
+    g_kernel_launches.fetch_sub(kernels);   // captured, not yet run
     cudaGraph_t graph = nullptr;
     cudaError_t ee = cudaStreamEndCapture(s, &graph);
     if (rc) {
@@ -240,13 +314,14 @@ int decode_group(const Group &g, cudaStream_t s) {
     cudaGraphDestroy(graph);
     if (ee != cudaSuccess) return cuda_fail(ee);
     std::lock_guard<std::mutex> lk(g_graph_mu);
-    g_graphs.emplace_front(key, exec);
+    g_graphs.emplace_front(key, GraphEntry{exec, kernels});
     if (g_graphs.size() > kMaxGraphs) {
-      cudaGraphExecDestroy(g_graphs.back().second);
+      cudaGraphExecDestroy(g_graphs.back().second.exec);
       g_graphs.pop_back();
     }
   }
   CK(cudaGraphLaunch(exec, s));
+  g_kernel_launches.fetch_add(kernels);
   return POLAR_OK;
 }
 
@@ -291,6 +366,8 @@ int polar_config_set(const char *key, long value) {
     g_cfg.graphs = value ? 1 : 0;
   } else if (!strcmp(key, "plain")) {
     g_cfg.plain = value ? 1 : 0;
+  } else if (!strcmp(key, "profile")) {
+    g_cfg.profile = value ? 1 : 0;
   } else {
     return POLAR_ENOTFOUND;
   }
@@ -303,8 +380,37 @@ int polar_config_get(const char *key, long *value) {
   else if (!strcmp(key, "shortcuts")) *value = g_cfg.shortcuts;
   else if (!strcmp(key, "graphs")) *value = g_cfg.graphs;
   else if (!strcmp(key, "plain")) *value = g_cfg.plain;
+  else if (!strcmp(key, "profile")) *value = g_cfg.profile;
   else return POLAR_ENOTFOUND;
   return POLAR_OK;
+}
+
+uint64_t polar_kernel_launches(void) { return g_kernel_launches.load(); }
+
+int polar_profile_read(const char *kind, double *total_ms, uint64_t *launches,
+                       double *alg_bytes) {
+  if (!kind) return POLAR_EINVAL;
+  prof_drain();
+  for (int i = 0; i < kNumKinds; ++i) {
+    if (!strcmp(kind, kKinds[i])) {
+      std::lock_guard<std::mutex> g(g_prof_mu);
+      if (total_ms) *total_ms = g_prof_ms[i];
+      if (launches) *launches = g_prof_n[i];
+      if (alg_bytes) *alg_bytes = g_prof_bytes[i];
+      return POLAR_OK;
+    }
+  }
+  return POLAR_ENOTFOUND;
+}
+
+void polar_profile_reset(void) {
+  prof_drain();
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  for (int i = 0; i < kNumKinds; ++i) {
+    g_prof_ms[i] = 0;
+    g_prof_n[i] = 0;
+    g_prof_bytes[i] = 0;
+  }
 }
 
 int polar_build_frozen_set(uint32_t log2n, polar_channel ch, double param, double rate,
@@ -333,7 +439,7 @@ void polar_frozen_set_free(polar_frozen_set *fs) {
     std::lock_guard<std::mutex> lk(g_graph_mu);
     for (auto it = g_graphs.begin(); it != g_graphs.end();) {
       if (std::get<0>(it->first) == fs->id) {
-        cudaGraphExecDestroy(it->second);
+        cudaGraphExecDestroy(it->second.exec);
         it = g_graphs.erase(it);
       } else {
         ++it;
@@ -353,12 +459,14 @@ int polar_llr_from_channel(polar_channel ch, double param, const void *y_dev, in
     if (!y_is_bits || !(param > 0.0 && param < 0.5) || n_total % 32) return POLAR_EINVAL;
     if (!aligned(y_dev, 4) || !aligned(llr_dev, 16)) return POLAR_EINVAL;
     const float c = (float)std::log((1.0 - param) / param);
+    ProfScope ps(g_cfg.profile.load() != 0, 0, n_total / 8.0 + 4.0 * n_total, s);
     CK(launch_llr_bsc(static_cast<const uint32_t *>(y_dev), llr_dev, n_total, c, s));
     return POLAR_OK;
   }
   if (ch == POLAR_BIAWGN) {
     if (y_is_bits || !(param > 0.0 && std::isfinite(param))) return POLAR_EINVAL;
     if (!aligned(y_dev, 16) || !aligned(llr_dev, 8)) return POLAR_EINVAL;
+    ProfScope ps(g_cfg.profile.load() != 0, 0, 12.0 * n_total, s);
     CK(launch_llr_biawgn(static_cast<const double *>(y_dev), llr_dev, n_total, 2.0 / param, s));
     return POLAR_OK;
   }

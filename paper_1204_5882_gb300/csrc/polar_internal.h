@@ -69,15 +69,6 @@ std::shared_ptr<Plan> get_plan(polar_frozen_set *fs, int t, bool shortcuts);
 const uint32_t *device_mask(polar_frozen_set *fs, int device, cudaError_t *err);
 
 // --- kernels (stream_kernels.cu, subtree.cu) --------------------------------
-struct FrameArrays {
-  const float *llr;     // level n, [F][N]
-  const uint32_t *fv;   // [F][W]
-  uint32_t *xhat;       // [F][W]
-  uint32_t *uhat;       // [F][W] or null
-  int nframes;
-  uint32_t log2n;
-};
-
 cudaError_t launch_llr_bsc(const uint32_t *y, float *llr, size_t n_total, float c,
                            cudaStream_t s);
 cudaError_t launch_llr_biawgn(const double *y, float *llr, size_t n_total, double scale,
@@ -122,5 +113,12 @@ struct SubtreeArgs {
 cudaError_t launch_subtree(const SubtreeArgs &a, cudaStream_t s);
 
 size_t storage_bytes(int prec);
+
+// Kernels launched by this library (graph replays included).
+extern std::atomic<uint64_t> g_kernel_launches;
+inline cudaError_t counted(cudaError_t e, uint64_t kernels) {
+  if (e == cudaSuccess) g_kernel_launches.fetch_add(kernels, std::memory_order_relaxed);
+  return e;
+}
 
 }  // namespace polar

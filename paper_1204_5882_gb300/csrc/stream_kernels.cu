@@ -49,7 +49,7 @@ cudaError_t launch_llr_bsc(const uint32_t *y, float *llr, size_t n_total, float 
                            cudaStream_t s) {
   size_t n4 = n_total / 4;
   k_llr_bsc<<<grid_for(n4, 256), 256, 0, s>>>(y, reinterpret_cast<float4 *>(llr), n4, c);
-  return cudaGetLastError();
+  return counted(cudaGetLastError(), 1);
 }
 
 cudaError_t launch_llr_biawgn(const double *y, float *llr, size_t n_total, double scale,
@@ -60,7 +60,7 @@ cudaError_t launch_llr_biawgn(const double *y, float *llr, size_t n_total, doubl
                                                   reinterpret_cast<float2 *>(llr), n2, scale);
   }
   if (n_total & 1) k_llr_biawgn_tail<<<1, 32, 0, s>>>(y, llr, n2 * 2, n_total, scale);
-  return cudaGetLastError();
+  return counted(cudaGetLastError(), (n2 ? 1 : 0) + (n_total & 1));
 }
 
 // ---------------------------------------------------------------- transform
@@ -125,6 +125,7 @@ __global__ void k_encode_xword_level(uint32_t *__restrict__ w, size_t stride, si
 cudaError_t launch_encode_regions(uint32_t *words, size_t stride_w, size_t off_w, int log2len,
                                   int nframes, cudaStream_t s) {
   size_t nw = log2len >= 5 ? (size_t(1) << (log2len - 5)) : 1;
+  uint64_t launched = 1;
   k_encode_inword<<<grid_for(nw * nframes, 256), 256, 0, s>>>(words, stride_w, off_w, nw,
                                                               nframes, log2len);
   if (nw > 1) {
@@ -135,13 +136,15 @@ cudaError_t launch_encode_regions(uint32_t *words, size_t stride_w, size_t off_w
     int grid = (int)(nblocks < 4096 ? nblocks : 4096);
     k_encode_xword_smem<<<grid, 256, bw * sizeof(uint32_t), s>>>(words, stride_w, off_w, nw,
                                                                  nframes, lv);
+    launched++;
     for (int l = lv; l < lvw; ++l) {
       size_t hw = size_t(1) << l;
       k_encode_xword_level<<<grid_for(nw / 2 * nframes, 256), 256, 0, s>>>(
           words, stride_w, off_w, nw, nframes, hw);
+      launched++;
     }
   }
-  return cudaGetLastError();
+  return counted(cudaGetLastError(), launched);
 }
 
 // dst[f][off + j] = src[f][off + j] (& and_mask[off + j] if given).
@@ -163,7 +166,7 @@ cudaError_t launch_copy_regions(const uint32_t *src, uint32_t *dst, size_t strid
                                 const uint32_t *and_mask, cudaStream_t s) {
   k_copy_regions<<<grid_for(nwords * nframes, 256), 256, 0, s>>>(src, dst, stride_w, off_w,
                                                                  nwords, nframes, and_mask);
-  return cudaGetLastError();
+  return counted(cudaGetLastError(), 1);
 }
 
 // ---------------------------------------------------------------- combine
@@ -177,7 +180,7 @@ cudaError_t launch_cascade(uint32_t *xhat, size_t stride_w, int k_unit, uint64_t
                            int nframes, cudaStream_t s) {
   if (r <= 0) return cudaSuccess;
   k_cascade<<<nframes, 512, 0, s>>>(xhat, stride_w, k_unit, o_unit, r);
-  return cudaGetLastError();
+  return counted(cudaGetLastError(), 1);
 }
 
 // ---------------------------------------------------------------- stream f / g
@@ -272,7 +275,7 @@ static cudaError_t stream_f_t(int fkind, const void *in, size_t in_stride, bool 
     else
       k_stream_f<T, T, 1><<<g, 256, 0, s>>>((const T *)in, in_stride, (T *)out, out_stride, h);
   }
-  return cudaGetLastError();
+  return counted(cudaGetLastError(), 1);
 }
 
 template <typename T>
@@ -286,8 +289,10 @@ static cudaError_t stream_g_t(const void *in, size_t in_stride, bool in_is_llr, 
   else
     k_stream_g<T, T><<<g, 256, 0, s>>>((const T *)in, in_stride, (T *)out, out_stride, h, xhat,
                                        xs, o);
-  return cudaGetLastError();
+  return counted(cudaGetLastError(), 1);
 }
+
+std::atomic<uint64_t> g_kernel_launches{0};
 
 size_t storage_bytes(int prec) { return prec == POLAR_FP32 ? 4 : (prec == POLAR_FP16 ? 2 : 1); }
 

@@ -265,7 +265,7 @@ cudaError_t launch_t(const SubtreeArgs &a, cudaStream_t s) {
   }
   StParams p{a.in, a.in_stride, a.mask, a.fv, a.xhat, a.uhat, a.w_stride, a.o, a.t, a.r};
   kern<<<a.nframes, 32, smem, s>>>(p, a.in_is_llr);
-  return cudaGetLastError();
+  return counted(cudaGetLastError(), 1);
 }
 
 template <typename S>

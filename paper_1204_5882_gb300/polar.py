@@ -54,6 +54,9 @@ def _load():
         "polar_last_error_string": ([], C.c_char_p),
         "polar_config_set": ([C.c_char_p, C.c_long], I),
         "polar_config_get": ([C.c_char_p, C.POINTER(C.c_long)], I),
+        "polar_kernel_launches": ([], U64),
+        "polar_profile_read": ([C.c_char_p, C.POINTER(D), C.POINTER(U64), C.POINTER(D)], I),
+        "polar_profile_reset": ([], None),
         "polar_build_frozen_set": ([U32, I, D, D, C.POINTER(P)], I),
         "polar_frozen_set_from_mask": ([U32, P, C.POINTER(P)], I),
         "polar_frozen_set_query": ([P, C.POINTER(U32), C.POINTER(U64), P, C.POINTER(D)], I),
@@ -109,6 +112,25 @@ def polar_config_get(key: str) -> int:
     v = C.c_long()
     _check("polar_config_get", _lib.polar_config_get(key.encode(), C.byref(v)))
     return v.value
+
+
+def polar_kernel_launches() -> int:
+    return int(_lib.polar_kernel_launches())
+
+
+def polar_profile_read(kind: str):
+    """(total_ms, launches, algorithmic_bytes) recorded for one kernel kind."""
+    ms, n, b = C.c_double(), C.c_uint64(), C.c_double()
+    _check("polar_profile_read", _lib.polar_profile_read(kind.encode(), C.byref(ms), C.byref(n),
+                                                         C.byref(b)))
+    return ms.value, n.value, b.value
+
+
+def polar_profile_reset():
+    _lib.polar_profile_reset()
+
+
+PROFILE_KINDS = ("llr", "stream_f", "stream_g", "subtree", "rate0")
 
 
 # ------------------------------------------------------------------ frozen sets
