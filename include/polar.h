@@ -203,6 +203,41 @@ typedef struct {
 int polar_sc_decode_batch(int nframes, const polar_frame_desc *frames,
                           polar_fkind fkind, polar_prec prec, void *stream);
 
+/* ------------------------------------------------- decoding, no allocation */
+
+/* Same decode as polar_sc_decode_many, for callers that cannot allocate
+ * device memory: processes whose device memory is all owned by another
+ * framework's fixed-size pool, latency-critical loops that cannot afford the
+ * device synchronisation cudaMalloc and cudaFree imply, and long-running
+ * services that must not meet an out-of-memory error mid-session.  The paper
+ * has no counterpart; this is a deployment variant.
+ *
+ * It calls no cudaMalloc, cudaFree or other allocating routine and builds no
+ * CUDA graph: the device copy of the frozen mask and the level scratch live
+ * in one fixed, file-scope device array of polar_static_scratch_bytes()
+ * bytes (16 MiB), which every GPU that loads this library holds until the
+ * process exits.  The caller still passes all inputs and outputs.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - Capacity: the mask (N/8 bytes, rounded up to 256) plus
+ *     nframes * (N - 2^t) * bytes(prec) of levels must fit, t being the
+ *     "subtree_log2" setting (e.g. up to 3 frames of 2^20 or 1 frame of 2^22
+ *     in FP32 at t = 13).  Larger requests return POLAR_EINVAL before any
+ *     launch, with the sizes in polar_last_error_string().
+ *   - Every call on a device shares the one array and leaves its contents
+ *     behind; the mask is rewritten each call and every scratch level is
+ *     written before it is read.  Calls whose work overlaps on the GPU (other
+ *     streams, other host threads) race on the array: serialise them.
+ * Launches are eager (the "graphs" option is ignored); results are identical
+ * to polar_sc_decode_many. */
+int polar_sc_decode_many_noalloc(const polar_frozen_set *fs, int nframes,
+                                 const float *llr_dev, const uint32_t *frozen_vals_dev,
+                                 uint32_t *xhat_dev, uint32_t *uhat_dev,
+                                 polar_fkind fkind, polar_prec prec, void *stream);
+
+/* Size in bytes of the static array behind polar_sc_decode_many_noalloc. */
+size_t polar_static_scratch_bytes(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -336,6 +336,40 @@ int check_group(const Group &g) {
 
 }  // namespace
 
+namespace polar {
+
+// Levels t..n-1 of nframes frames at the current "subtree_log2", in bytes.
+size_t level_scratch_bytes(const polar_frozen_set *fs, int nframes, int prec, int *t_out) {
+  const int n = (int)fs->log2n;
+  const int t = std::min<int>(n, (int)g_cfg.subtree_log2.load());
+  if (t_out) *t_out = t;
+  if (n <= t) return 0;
+  return (size_t)nframes * ((size_t(1) << n) - (size_t(1) << t)) * storage_bytes(prec);
+}
+
+// One batch decoded with launches only: the caller supplies the device mask
+// and the level scratch, so no device memory is allocated and no graph is
+// built.  Host-side the cached schedule of the frozen set is reused.
+int decode_with_scratch(const polar_frozen_set *fs_c, int nframes, const float *llr,
+                        const uint32_t *fv, uint32_t *xhat, uint32_t *uhat, int fkind, int prec,
+                        const uint32_t *dmask, void *scratch, size_t scratch_bytes,
+                        cudaStream_t s) {
+  polar_frozen_set *fs = const_cast<polar_frozen_set *>(fs_c);
+  Group g{fs, nframes, llr, fv, xhat, uhat, fkind, prec};
+  int rc = check_group(g);
+  if (rc) return rc;
+  int t = 0;
+  if (level_scratch_bytes(fs, nframes, prec, &t) > scratch_bytes) return POLAR_EINVAL;
+  const bool shortcuts = g_cfg.shortcuts.load() != 0;
+  std::shared_ptr<Plan> plan = get_plan(fs, t, shortcuts);
+  Exec x{plan.get(), &g, dmask, scratch, (int)fs->log2n, t};
+  return run_ops(x, s, false);
+}
+
+void set_last_error(const char *msg) { g_last_error = msg; }
+
+}  // namespace polar
+
 // ====================================================================== ABI
 extern "C" {
 

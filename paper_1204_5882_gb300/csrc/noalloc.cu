@@ -1,0 +1,89 @@
+// Decoding without any device allocation, for callers that cannot allocate
+// device memory themselves or through this library: processes whose device
+// memory is all owned by another framework's fixed-size pool, latency-
+// critical loops that cannot afford the implicit device synchronisation of
+// cudaMalloc / cudaFree, and long-running services that must not meet an
+// out-of-memory error in the middle of a session.
+//
+// The level scratch and the device copy of the frozen mask live in one
+// file-scope device array of fixed size.  Every GPU that loads this library
+// holds that array until the process exits.
+#include <cstdio>
+#include <mutex>
+
+#include "polar_internal.h"
+
+#define POLAR_STATIC_SCRATCH_BYTES (16u << 20)
+
+static __device__ __align__(256) unsigned char g_polar_static_scratch[POLAR_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void *g_static_ptr[kMaxDevices];
+
+// Device address of the array on the current device.  The host-side symbol
+// is only a stand-in and must never reach a kernel; the real address is
+// looked up once per device, with that device current.
+int static_scratch(int dev, unsigned char **out) {
+  if (dev < 0 || dev >= kMaxDevices) return POLAR_EINVAL;
+  std::lock_guard<std::mutex> g(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_polar_static_scratch);
+    if (e != cudaSuccess || !p) {
+      polar::set_last_error(cudaGetErrorString(e));
+      return POLAR_ECUDA;
+    }
+    g_static_ptr[dev] = p;
+  }
+  *out = static_cast<unsigned char *>(g_static_ptr[dev]);
+  return POLAR_OK;
+}
+
+}  // namespace
+
+extern "C" size_t polar_static_scratch_bytes(void) { return POLAR_STATIC_SCRATCH_BYTES; }
+
+extern "C" int polar_sc_decode_many_noalloc(const polar_frozen_set *fs, int nframes,
+                                            const float *llr_dev,
+                                            const uint32_t *frozen_vals_dev,
+                                            uint32_t *xhat_dev, uint32_t *uhat_dev,
+                                            polar_fkind fkind, polar_prec prec, void *stream) {
+  if (!fs || nframes < 1 || !llr_dev || !frozen_vals_dev || !xhat_dev) return POLAR_EINVAL;
+  if (prec != POLAR_FP32 && prec != POLAR_FP16) return POLAR_EINVAL;
+  const size_t mask_bytes = ((fs->mask.size() * sizeof(uint32_t)) + 255) & ~size_t(255);
+  const size_t level_bytes = polar::level_scratch_bytes(fs, nframes, (int)prec, nullptr);
+  if (mask_bytes + level_bytes > POLAR_STATIC_SCRATCH_BYTES) {
+    static thread_local char msg[160];
+    snprintf(msg, sizeof msg,
+             "noalloc decode needs %zu bytes of scratch; the static array holds %u bytes",
+             mask_bytes + level_bytes, (unsigned)POLAR_STATIC_SCRATCH_BYTES);
+    polar::set_last_error(msg);
+    return POLAR_EINVAL;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    polar::set_last_error(cudaGetErrorString(e));
+    return POLAR_ECUDA;
+  }
+  unsigned char *base = nullptr;
+  int rc = static_scratch(dev, &base);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // The mask is rewritten on every call: the array keeps whatever the last
+  // call on this device left there.  The level scratch needs no clearing:
+  // every level is written before it is read.
+  e = cudaMemcpyAsync(base, fs->mask.data(), fs->mask.size() * sizeof(uint32_t),
+                      cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) {
+    polar::set_last_error(cudaGetErrorString(e));
+    return POLAR_ECUDA;
+  }
+  return polar::decode_with_scratch(fs, nframes, llr_dev, frozen_vals_dev, xhat_dev, uhat_dev,
+                                    (int)fkind, (int)prec, reinterpret_cast<uint32_t *>(base),
+                                    base + mask_bytes, POLAR_STATIC_SCRATCH_BYTES - mask_bytes,
+                                    s);
+}

@@ -114,6 +114,14 @@ cudaError_t launch_subtree(const SubtreeArgs &a, cudaStream_t s);
 
 size_t storage_bytes(int prec);
 
+// api.cu: decoding with caller-provided device mask and level scratch.
+size_t level_scratch_bytes(const polar_frozen_set *fs, int nframes, int prec, int *t_out);
+int decode_with_scratch(const polar_frozen_set *fs, int nframes, const float *llr,
+                        const uint32_t *fv, uint32_t *xhat, uint32_t *uhat, int fkind, int prec,
+                        const uint32_t *dmask, void *scratch, size_t scratch_bytes,
+                        cudaStream_t s);
+void set_last_error(const char *msg);
+
 // Kernels launched by this library (graph replays included).
 extern std::atomic<uint64_t> g_kernel_launches;
 inline cudaError_t counted(cudaError_t e, uint64_t kernels) {

@@ -67,6 +67,8 @@ def _load():
         "polar_sc_decode": ([P, P, P, P, P, I, I, P], I),
         "polar_sc_decode_many": ([P, I, P, P, P, P, I, I, P], I),
         "polar_sc_decode_batch": ([I, C.POINTER(FrameDesc), I, I, P], I),
+        "polar_sc_decode_many_noalloc": ([P, I, P, P, P, P, I, I, P], I),
+        "polar_static_scratch_bytes": ([], SZ),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -215,6 +217,17 @@ def polar_sc_decode_batch(frames, fkind="minsum", prec="fp32", stream=None):
                            uh.data_ptr() if uh is not None else None)
     _check("polar_sc_decode_batch", _lib.polar_sc_decode_batch(
         len(frames), arr, FKIND[fkind], PREC[prec], _stream(stream)))
+
+
+def polar_sc_decode_many_noalloc(fs: FrozenSet, nframes: int, llr, fval, xhat, uhat=None,
+                                 fkind="minsum", prec="fp32", stream=None):
+    _check("polar_sc_decode_many_noalloc", _lib.polar_sc_decode_many_noalloc(
+        fs.handle, int(nframes), _ptr(llr), _ptr(fval), _ptr(xhat), _ptr(uhat), FKIND[fkind],
+        PREC[prec], _stream(stream)))
+
+
+def polar_static_scratch_bytes() -> int:
+    return int(_lib.polar_static_scratch_bytes())
 
 
 def exported_symbols():
