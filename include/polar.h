@@ -219,7 +219,8 @@ int polar_sc_decode_batch(int nframes, const polar_frame_desc *frames,
  * process exits.  The caller still passes all inputs and outputs.
  *   - The first call on a device looks up the array's device address (with
  *     that device current); make that first call before any stream capture.
- *   - Capacity: the mask (N/8 bytes, rounded up to 256) plus
+ *   - Capacity: the mask (N/8 bytes), the subtree node-class table (N/64
+ *     bytes when shortcuts are on), each rounded up to 256, plus
  *     nframes * (N - 2^t) * bytes(prec) of levels must fit, t being the
  *     "subtree_log2" setting (e.g. up to 3 frames of 2^20 or 1 frame of 2^22
  *     in FP32 at t = 13).  Larger requests return POLAR_EINVAL before any

@@ -51,6 +51,10 @@ def lib():
         for nm in ("or_sc_decode_f64", "or_sc_decode_f32"):
             getattr(L, nm).argtypes = [C.c_int, C.c_int, P, P, P, P, P, P]
             getattr(L, nm).restype = C.c_int
+        L.or_sc_decode_store.argtypes = [C.c_int, C.c_int, C.c_int, C.c_float, P, P, P, P, P, P]
+        L.or_sc_decode_store.restype = C.c_int
+        L.or_int8_scale.argtypes = [P, C.c_size_t, C.c_double]
+        L.or_int8_scale.restype = C.c_float
         L.or_bhatt_log_from.argtypes = [C.c_int, C.c_double, P]
         L.or_bhatt_log_bsc.argtypes = [C.c_int, C.c_double, P]
         L.or_ga_lnphi.argtypes = [C.c_double]
@@ -139,6 +143,32 @@ def sc_decode(llr, frozen, fval, fkind: str = "minsum", leaf: bool = False):
     rc = getattr(lib(), f"or_sc_decode_f{prec}")(
         n, FKIND[fkind], _p(llr), _p(fz), _p(fv), _p(u), _p(x),
         _p(lf) if leaf else None)
+    if rc != 0:
+        raise MemoryError("oracle decode failed")
+    return (u, x, lf) if leaf else (u, x)
+
+
+STORE = {"fp32": 0, "fp16": 1, "int8": 2}
+INT8_TARGET = 8.0
+
+
+def int8_scale(llr, target: float = INT8_TARGET) -> float:
+    """Per-frame power-of-two scale so that mean |L| * scale is near target."""
+    llr = np.ascontiguousarray(llr, dtype=np.float32)
+    return float(lib().or_int8_scale(_p(llr), llr.size, float(target)))
+
+
+def sc_decode_store(llr, frozen, fval, fkind: str = "minsum", store: str = "fp16",
+                    scale: float = 1.0, leaf: bool = False):
+    """SC with reduced-precision storage of every LLR (float arithmetic)."""
+    llr = np.ascontiguousarray(llr, dtype=np.float32)
+    n = log2_of(llr.size)
+    fz, fv = _bits(frozen), _bits(fval)
+    u = np.empty(llr.size, dtype=np.uint8)
+    x = np.empty(llr.size, dtype=np.uint8)
+    lf = np.empty(llr.size, dtype=np.float32) if leaf else None
+    rc = lib().or_sc_decode_store(n, FKIND[fkind], STORE[store], float(scale), _p(llr), _p(fz),
+                                  _p(fv), _p(u), _p(x), _p(lf) if leaf else None)
     if rc != 0:
         raise MemoryError("oracle decode failed")
     return (u, x, lf) if leaf else (u, x)

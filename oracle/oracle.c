@@ -175,6 +175,82 @@ OR_DEFINE_SC(double, f64, or_f_exact_f64, or_f_minsum_f64)
 OR_DEFINE_SC(float, f32, or_f_exact_f32, or_f_minsum_f32)
 
 /* ------------------------------------------------------------------------ */
+/* Reduced-precision storage of the LLRs (the paper's fixed-point decoder,  */
+/* Sec. 4, leaves the width open).  Reading: every LLR that is stored --    */
+/* the channel LLRs on entry and every f and g output -- is rounded to the  */
+/* storage format, while f and g themselves are evaluated in float:         */
+/*   store 1 (half): clamp to +-65504, round to nearest even half;         */
+/*   store 2 (int8): values are L * scale (scale a power of two chosen per  */
+/*                   frame), rounded to nearest even integer, clamped to    */
+/*                   +-127; exact f is evaluated on L = value / scale.      */
+/* store 0 is plain float storage (identical to or_sc_decode_f32).          */
+/* ------------------------------------------------------------------------ */
+static float q_store(float v, int store)
+{
+    if (store == 1) {
+        v = fminf(fmaxf(v, -65504.0f), 65504.0f);
+        return (float)(_Float16)v;
+    }
+    if (store == 2) return fminf(fmaxf(rintf(v), -127.0f), 127.0f);
+    return v;
+}
+
+static float f_store(float a, float b, int fkind, int store, float scale)
+{
+    if (!fkind) return q_store(or_f_minsum_f32(a, b), store);
+    if (store == 2) return q_store(scale * or_f_exact_f32(a / scale, b / scale), store);
+    return q_store(or_f_exact_f32(a, b), store);
+}
+
+static void sc_node_q(int k, const float *L, const uint8_t *frz, const uint8_t *fval,
+                      uint8_t *u, uint8_t *beta, int fkind, int store, float scale,
+                      float *scratch, float *leaf)
+{
+    if (k == 0) {
+        uint8_t d = frz[0] ? fval[0] : (uint8_t)(L[0] < 0.0f);
+        u[0] = d;
+        beta[0] = d;
+        if (leaf) leaf[0] = L[0];
+        return;
+    }
+    size_t h = (size_t)1 << (k - 1);
+    float *Lc = scratch;
+    for (size_t j = 0; j < h; j++) Lc[j] = f_store(L[j], L[j + h], fkind, store, scale);
+    sc_node_q(k - 1, Lc, frz, fval, u, beta, fkind, store, scale, scratch + h, leaf);
+    for (size_t j = 0; j < h; j++)
+        Lc[j] = q_store(beta[j] ? (L[j + h] - L[j]) : (L[j + h] + L[j]), store);
+    sc_node_q(k - 1, Lc, frz + h, fval + h, u + h, beta + h, fkind, store, scale, scratch + h,
+              leaf ? leaf + h : NULL);
+    for (size_t j = 0; j < h; j++) beta[j] ^= beta[j + h];
+}
+
+OR_API int or_sc_decode_store(int n, int fkind, int store, float scale, const float *llr,
+                              const uint8_t *frozen, const uint8_t *fval, uint8_t *u_hat,
+                              uint8_t *x_hat, float *leaf)
+{
+    size_t N = (size_t)1 << n;
+    float *buf = (float *)malloc(sizeof(float) * 2 * N);
+    if (!buf) return -1;
+    for (size_t i = 0; i < N; i++) buf[i] = q_store(store == 2 ? llr[i] * scale : llr[i], store);
+    sc_node_q(n, buf, frozen, fval, u_hat, x_hat, fkind, store, scale, buf + N, leaf);
+    free(buf);
+    return 0;
+}
+
+/* Per-frame int8 scale: the power of two s = 2^e, e = round(log2(target /  */
+/* mean |L|)), mean taken in double; s = 1 when every L is zero.            */
+OR_API float or_int8_scale(const float *llr, size_t n, double target)
+{
+    double acc = 0.0;
+    for (size_t i = 0; i < n; i++) acc += fabs((double)llr[i]);
+    if (!(acc > 0.0)) return 1.0f;
+    double e = nearbyint(log2(target / (acc / (double)n)));
+    if (e > 100) e = 100;
+    if (e < -100) e = -100;
+    return (float)ldexp(1.0, (int)e);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Frozen-set construction (Sec. 3: density evolution selects the frozen    */
 /* bits as the lowest-capacity bit-channels).  The paper uses the method of */
 /* Mori-Tanaka; this oracle implements the two standard substitutes:        */

@@ -153,6 +153,7 @@ struct Exec {
   const uint32_t *dmask;
   void *ws;
   int n, t;
+  const uint32_t *dclass;   // class table (shortcuts, t >= 5) or null
 };
 
 inline void *level_ptr(const Exec &x, int k) {
@@ -193,6 +194,7 @@ int run_ops(const Exec &x, cudaStream_t s, bool prof) {
         a.in = a.in_is_llr ? static_cast<const void *>(g.llr) : level_ptr(x, t);
         a.in_stride = a.in_is_llr ? N : (size_t(1) << t);
         a.mask = x.dmask;
+        a.cls = x.dclass ? x.dclass + (op.o >> t) * 2 * class_words(t) : nullptr;
         a.fv = g.fv;
         a.xhat = g.xhat;
         a.uhat = g.uhat;
@@ -248,6 +250,11 @@ int decode_group(const Group &g, cudaStream_t s) {
   const uint32_t *dmask = device_mask(fs, dev, &e);
   if (!dmask) return e == cudaErrorMemoryAllocation ? POLAR_ENOMEM : cuda_fail(e);
   std::shared_ptr<Plan> plan = get_plan(fs, t, shortcuts);
+  const uint32_t *dclass = nullptr;
+  if (shortcuts && t >= 5) {
+    dclass = device_class_table(fs, dev, t, &e);
+    if (!dclass) return e == cudaErrorMemoryAllocation ? POLAR_ENOMEM : cuda_fail(e);
+  }
   const int F = plain ? 1 : g.nframes;
   size_t ws_bytes = n > t ? (size_t)F * ((size_t(1) << n) - (size_t(1) << t)) * storage_bytes(g.prec)
                           : 0;
@@ -266,13 +273,13 @@ int decode_group(const Group &g, cudaStream_t s) {
       one.fv = g.fv + (size_t)f * W;
       one.xhat = g.xhat + (size_t)f * W;
       one.uhat = g.uhat ? g.uhat + (size_t)f * W : nullptr;
-      Exec x{plan.get(), &one, dmask, ws, n, t};
+      Exec x{plan.get(), &one, dmask, ws, n, t, dclass};
       rc = run_ops(x, s, g_cfg.profile.load() != 0);
       if (rc) return rc;
     }
     return POLAR_OK;
   }
-  Exec x{plan.get(), &g, dmask, ws, n, t};
+  Exec x{plan.get(), &g, dmask, ws, n, t, dclass};
   const bool prof = g_cfg.profile.load() != 0;
   bool use_graph = graphs && !prof && s != nullptr;
   if (use_graph) {
@@ -350,10 +357,12 @@ size_t level_scratch_bytes(const polar_frozen_set *fs, int nframes, int prec, in
 // One batch decoded with launches only: the caller supplies the device mask
 // and the level scratch, so no device memory is allocated and no graph is
 // built.  Host-side the cached schedule of the frozen set is reused.
+bool shortcuts_enabled() { return g_cfg.shortcuts.load() != 0; }
+
 int decode_with_scratch(const polar_frozen_set *fs_c, int nframes, const float *llr,
                         const uint32_t *fv, uint32_t *xhat, uint32_t *uhat, int fkind, int prec,
-                        const uint32_t *dmask, void *scratch, size_t scratch_bytes,
-                        cudaStream_t s) {
+                        const uint32_t *dmask, const uint32_t *dclass, void *scratch,
+                        size_t scratch_bytes, cudaStream_t s) {
   polar_frozen_set *fs = const_cast<polar_frozen_set *>(fs_c);
   Group g{fs, nframes, llr, fv, xhat, uhat, fkind, prec};
   int rc = check_group(g);
@@ -361,8 +370,9 @@ int decode_with_scratch(const polar_frozen_set *fs_c, int nframes, const float *
   int t = 0;
   if (level_scratch_bytes(fs, nframes, prec, &t) > scratch_bytes) return POLAR_EINVAL;
   const bool shortcuts = g_cfg.shortcuts.load() != 0;
+  if (shortcuts && t >= 5 && !dclass) return POLAR_EINVAL;
   std::shared_ptr<Plan> plan = get_plan(fs, t, shortcuts);
-  Exec x{plan.get(), &g, dmask, scratch, (int)fs->log2n, t};
+  Exec x{plan.get(), &g, dmask, scratch, (int)fs->log2n, t, shortcuts && t >= 5 ? dclass : nullptr};
   return run_ops(x, s, false);
 }
 

@@ -281,4 +281,59 @@ const uint32_t *device_mask(polar_frozen_set *fs, int device, cudaError_t *err) 
   return d;
 }
 
+static std::vector<uint32_t> build_class_table(const polar_frozen_set *fs, int t) {
+  const int n = (int)fs->log2n;
+  const uint32_t CW = class_words(t);
+  const uint64_t nsub = t <= n ? (uint64_t(1) << (n - t)) : 1;
+  std::vector<uint32_t> tab(nsub * 2 * CW, 0u);
+  if (t < 5) return tab;
+  for (uint64_t j = 0; j < nsub; ++j) {
+    uint32_t *r0 = tab.data() + j * 2 * CW, *r1 = r0 + CW;
+    for (int k = 5; k <= t; ++k) {
+      for (uint64_t q = 0; q < (uint64_t(1) << (t - k)); ++q) {
+        const NodeClass c = node_class_host(fs, k, (j << t) + (q << k));
+        const uint64_t i = (uint64_t(1) << (t - k)) + q;
+        if (c == NODE_RATE0) r0[i >> 5] |= 1u << (i & 31);
+        if (c == NODE_RATE1) r1[i >> 5] |= 1u << (i & 31);
+      }
+    }
+  }
+  return tab;
+}
+
+std::shared_ptr<std::vector<uint32_t>> class_table_host(polar_frozen_set *fs, int t) {
+  std::lock_guard<std::mutex> g(fs->mu);
+  auto it = fs->hclass.find(t);
+  if (it != fs->hclass.end()) return it->second;
+  auto tab = std::make_shared<std::vector<uint32_t>>(build_class_table(fs, t));
+  fs->hclass[t] = tab;
+  return tab;
+}
+
+const uint32_t *device_class_table(polar_frozen_set *fs, int device, int t, cudaError_t *err) {
+  *err = cudaSuccess;
+  {
+    std::lock_guard<std::mutex> g(fs->mu);
+    auto it = fs->dclass.find({device, t});
+    if (it != fs->dclass.end()) return it->second;
+  }
+  std::shared_ptr<std::vector<uint32_t>> tab = class_table_host(fs, t);
+  uint32_t *d = nullptr;
+  *err = cudaMalloc(&d, tab->size() * sizeof(uint32_t));
+  if (*err != cudaSuccess) return nullptr;
+  *err = cudaMemcpy(d, tab->data(), tab->size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+  if (*err != cudaSuccess) {
+    cudaFree(d);
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> g(fs->mu);
+  auto it = fs->dclass.find({device, t});
+  if (it != fs->dclass.end()) {
+    cudaFree(d);
+    return it->second;
+  }
+  fs->dclass[{device, t}] = d;
+  return d;
+}
+
 }  // namespace polar

@@ -53,13 +53,21 @@ extern "C" int polar_sc_decode_many_noalloc(const polar_frozen_set *fs, int nfra
                                             polar_fkind fkind, polar_prec prec, void *stream) {
   if (!fs || nframes < 1 || !llr_dev || !frozen_vals_dev || !xhat_dev) return POLAR_EINVAL;
   if (prec != POLAR_FP32 && prec != POLAR_FP16) return POLAR_EINVAL;
+  polar_frozen_set *fsm = const_cast<polar_frozen_set *>(fs);
   const size_t mask_bytes = ((fs->mask.size() * sizeof(uint32_t)) + 255) & ~size_t(255);
-  const size_t level_bytes = polar::level_scratch_bytes(fs, nframes, (int)prec, nullptr);
-  if (mask_bytes + level_bytes > POLAR_STATIC_SCRATCH_BYTES) {
+  int t = 0;
+  const size_t level_bytes = polar::level_scratch_bytes(fs, nframes, (int)prec, &t);
+  // node-class table of the subtrees, when the shortcuts use one
+  std::shared_ptr<std::vector<uint32_t>> ctab;
+  if (polar::shortcuts_enabled() && t >= 5) ctab = polar::class_table_host(fsm, t);
+  const size_t class_bytes =
+      ctab ? ((ctab->size() * sizeof(uint32_t)) + 255) & ~size_t(255) : 0;
+  const size_t need = mask_bytes + class_bytes + level_bytes;
+  if (need > POLAR_STATIC_SCRATCH_BYTES) {
     static thread_local char msg[160];
     snprintf(msg, sizeof msg,
              "noalloc decode needs %zu bytes of scratch; the static array holds %u bytes",
-             mask_bytes + level_bytes, (unsigned)POLAR_STATIC_SCRATCH_BYTES);
+             need, (unsigned)POLAR_STATIC_SCRATCH_BYTES);
     polar::set_last_error(msg);
     return POLAR_EINVAL;
   }
@@ -73,17 +81,22 @@ extern "C" int polar_sc_decode_many_noalloc(const polar_frozen_set *fs, int nfra
   int rc = static_scratch(dev, &base);
   if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // The mask is rewritten on every call: the array keeps whatever the last
-  // call on this device left there.  The level scratch needs no clearing:
-  // every level is written before it is read.
+  // The mask and the class table are rewritten on every call: the array
+  // keeps whatever the last call on this device left there.  The level
+  // scratch needs no clearing: every level is written before it is read.
   e = cudaMemcpyAsync(base, fs->mask.data(), fs->mask.size() * sizeof(uint32_t),
                       cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && ctab)
+    e = cudaMemcpyAsync(base + mask_bytes, ctab->data(), ctab->size() * sizeof(uint32_t),
+                        cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) {
     polar::set_last_error(cudaGetErrorString(e));
     return POLAR_ECUDA;
   }
-  return polar::decode_with_scratch(fs, nframes, llr_dev, frozen_vals_dev, xhat_dev, uhat_dev,
-                                    (int)fkind, (int)prec, reinterpret_cast<uint32_t *>(base),
-                                    base + mask_bytes, POLAR_STATIC_SCRATCH_BYTES - mask_bytes,
-                                    s);
+  const size_t head = mask_bytes + class_bytes;
+  return polar::decode_with_scratch(
+      fs, nframes, llr_dev, frozen_vals_dev, xhat_dev, uhat_dev, (int)fkind, (int)prec,
+      reinterpret_cast<uint32_t *>(base),
+      ctab ? reinterpret_cast<uint32_t *>(base + mask_bytes) : nullptr, base + head,
+      POLAR_STATIC_SCRATCH_BYTES - head, s);
 }

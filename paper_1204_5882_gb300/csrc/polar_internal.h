@@ -55,6 +55,8 @@ struct polar_frozen_set {
   std::vector<uint32_t> mask;   // max(1, N/32) words, bit set = frozen
   std::mutex mu;
   std::map<int, uint32_t *> dmask;                        // device -> mask copy
+  std::map<std::pair<int, int>, uint32_t *> dclass;       // (device, t) -> class table
+  std::map<int, std::shared_ptr<std::vector<uint32_t>>> hclass;   // t -> host class table
   std::map<std::pair<int, int>, std::shared_ptr<polar::Plan>> plans;  // (t, shortcuts)
 };
 
@@ -67,6 +69,12 @@ int frozen_set_from_mask(uint32_t log2n, const uint32_t *mask, polar_frozen_set 
 NodeClass node_class_host(const polar_frozen_set *fs, int k, uint64_t o);
 std::shared_ptr<Plan> get_plan(polar_frozen_set *fs, int t, bool shortcuts);
 const uint32_t *device_mask(polar_frozen_set *fs, int device, cudaError_t *err);
+// Node-class table of every subtree of 2^t leaves (levels 5..t): per subtree
+// class_words(t) words of "rate 0" bits then as many of "rate 1" bits; node
+// (k, q) of a subtree is bit 2^(t-k) + q.
+inline uint32_t class_words(int t) { return t >= 9 ? (1u << (t - 9)) : 1u; }
+std::shared_ptr<std::vector<uint32_t>> class_table_host(polar_frozen_set *fs, int t);
+const uint32_t *device_class_table(polar_frozen_set *fs, int device, int t, cudaError_t *err);
 
 // --- kernels (stream_kernels.cu, subtree.cu) --------------------------------
 cudaError_t launch_llr_bsc(const uint32_t *y, float *llr, size_t n_total, float c,
@@ -97,6 +105,7 @@ struct SubtreeArgs {
   const void *in;        // level-t LLRs of every frame (or the channel LLRs)
   size_t in_stride;      // elements between frames
   bool in_is_llr;        // in is the float channel LLR array (level n == t)
+  const uint32_t *cls;   // device class table of this subtree (levels 5..t) or null
   const uint32_t *mask;  // device frozen mask (whole code)
   const uint32_t *fv;
   uint32_t *xhat;
@@ -118,8 +127,9 @@ size_t storage_bytes(int prec);
 size_t level_scratch_bytes(const polar_frozen_set *fs, int nframes, int prec, int *t_out);
 int decode_with_scratch(const polar_frozen_set *fs, int nframes, const float *llr,
                         const uint32_t *fv, uint32_t *xhat, uint32_t *uhat, int fkind, int prec,
-                        const uint32_t *dmask, void *scratch, size_t scratch_bytes,
-                        cudaStream_t s);
+                        const uint32_t *dmask, const uint32_t *dclass, void *scratch,
+                        size_t scratch_bytes, cudaStream_t s);
+bool shortcuts_enabled();
 void set_last_error(const char *msg);
 
 // Kernels launched by this library (graph replays included).

@@ -13,6 +13,13 @@
 //                        reproduces sgn(b), so each leaf's decision is the
 //                        hard decision of its input; a zero input falls back
 //                        to the full recursion.
+//
+// With shortcuts on, node classes of the levels 5..t come from a table the
+// host precomputes per subtree, and every mixed node of 32 leaves is decoded
+// in registers by a fully unrolled recursion (all lanes run it redundantly;
+// no shuffles, no shared-memory round trips below 32 leaves).  The plain
+// variant (shortcuts off) runs every level lane-parallel through shared
+// memory down to single leaves.
 #include "device_common.cuh"
 #include "polar_internal.h"
 
@@ -25,6 +32,7 @@ constexpr uint32_t FULL = 0xFFFFFFFFu;
 struct StParams {
   const void *in;
   size_t in_stride;
+  const uint32_t *cls;   // class table of this subtree (levels 5..t), or null
   const uint32_t *mask;
   const uint32_t *fv;
   uint32_t *xhat;
@@ -35,13 +43,115 @@ struct StParams {
   int r;
 };
 
+// Value as it would be after a store to S (storage rounding / saturation),
+// so that register-resident levels behave like stored ones.
+template <typename S>
+__device__ __forceinline__ float rnd(float v);
+template <>
+__device__ __forceinline__ float rnd<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float rnd<__half>(float v) {
+  return __half2float(__float2half_rn(fminf(fmaxf(v, -65504.0f), 65504.0f)));
+}
+
+// g with the partial sum taken from bit j of a word: b + a or b - a (the
+// latter as b + (-a), which IEEE addition makes identical).
+__device__ __forceinline__ float g_bit(float a, float b, uint32_t word, int j) {
+  return b + __uint_as_float(__float_as_uint(a) ^ ((word << (31 - j)) & 0x80000000u));
+}
+
+// SC over a node of 2^K leaves held in registers: returns beta (2^K bits)
+// and u_hat in `u`.  frz / fv are the node's mask and frozen values in the
+// low 2^K bits.  CHECK: test the node itself for rate 0 / rate 1 first.
+template <int K, int FK, bool CHECK, typename S>
+struct Dec {
+  static constexpr int N = 1 << K, H = N / 2;
+  static __device__ __forceinline__ uint32_t run(const float (&a)[N], uint32_t frz, uint32_t fv,
+                                                 uint32_t &u) {
+    constexpr uint32_t M = (N == 32) ? 0xFFFFFFFFu : ((1u << N) - 1u);
+    constexpr uint32_t MH = (1u << H) - 1u;
+    if (CHECK) {
+      if (frz == M) {
+        u = fv;
+        return encode_word(fv, K);
+      }
+      if (frz == 0u) {
+        float mn = fabsf(a[0]);
+        uint32_t b = __float_as_uint(a[0]) >> 31;
+#pragma unroll
+        for (int j = 1; j < N; ++j) {
+          mn = fminf(mn, fabsf(a[j]));
+          b |= (__float_as_uint(a[j]) >> 31) << j;
+        }
+        if (mn > 0.0f) {           // no zero input: signs are the decisions
+          u = encode_word(b, K);
+          return b;
+        }
+      }
+    }
+    float l[H];
+    uint32_t uL, bL;
+    const uint32_t fzL = frz & MH, fvL = fv & MH;
+    if (fzL == MH) {               // rate-0 left child: its f is never needed
+      uL = fvL;
+      bL = encode_word(fvL, K - 1);
+    } else {
+#pragma unroll
+      for (int j = 0; j < H; ++j) l[j] = rnd<S>(f_op<FK>(a[j], a[j + H]));
+      bL = Dec<K - 1, FK, true, S>::run(l, fzL, fvL, uL);
+    }
+#pragma unroll
+    for (int j = 0; j < H; ++j) l[j] = rnd<S>(g_bit(a[j], a[j + H], bL, j));
+    uint32_t uR;
+    const uint32_t bR = Dec<K - 1, FK, true, S>::run(l, frz >> H, fv >> H, uR);
+    u = uL | (uR << H);
+    return (bL ^ bR) | (bR << H);
+  }
+};
+
+template <int FK, bool CHECK, typename S>
+struct Dec<0, FK, CHECK, S> {
+  static __device__ __forceinline__ uint32_t run(const float (&a)[1], uint32_t frz, uint32_t fv,
+                                                 uint32_t &u) {
+    u = (frz & 1u) ? (fv & 1u) : (a[0] < 0.0f ? 1u : 0u);
+    return u;
+  }
+};
+
 template <typename S>
 struct Warp {
   S *L;
   uint32_t *beta, *uh, *msk, *fvw;
-  int lane;
+  const uint32_t *cr0, *cr1;   // class table: bit 2^(t-k) + (o >> k) for level k >= 5
+  int lane, t;
 
   __device__ __forceinline__ S *lvl(int k) const { return L + (1u << k); }
+
+  // Class of a node of level k >= 5 from the table.
+  __device__ __forceinline__ int cls_tab(int k, uint32_t o) const {
+    uint32_t i = (1u << (t - k)) + (o >> k);
+    uint32_t b0 = (cr0[i >> 5] >> (i & 31)) & 1u, b1 = (cr1[i >> 5] >> (i & 31)) & 1u;
+    return b0 ? NODE_RATE0 : (b1 ? NODE_RATE1 : NODE_MIXED);
+  }
+
+  // Mixed node of 2^K leaves (K <= 5) at leaf o, decoded in registers.
+  template <int K, int FK, bool CHECK>
+  __device__ void leafblock(uint32_t o) const {
+    constexpr int N = 1 << K;
+    const S *src = lvl(K);
+    float a[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) a[j] = Store<S>::ld(src + j);
+    const uint32_t m = N == 32 ? 0xFFFFFFFFu : ((1u << N) - 1u);
+    const uint32_t sh = o & 31;
+    uint32_t u;
+    uint32_t b = Dec<K, FK, CHECK, S>::run(a, (msk[o >> 5] >> sh) & m, (fvw[o >> 5] >> sh) & m, u);
+    if (lane == 0) {
+      insert(beta, o, N, b);
+      insert(uh, o, N, u);
+    }
+    __syncwarp();
+  }
 
   __device__ int node_class(int k, uint32_t o) const {
     if (k < 5) {
@@ -139,23 +249,52 @@ struct Warp {
 
   template <int FK>
   __device__ void f(int k) const {
-    const S *a = lvl(k);
-    S *c = lvl(k - 1);
+    const S *__restrict__ a = lvl(k);
+    S *__restrict__ c = lvl(k - 1);
     const uint32_t h = 1u << (k - 1);
-    for (uint32_t i = lane; i < h; i += 32)
-      Store<S>::st(c + i, f_op<FK>(Store<S>::ld(a + i), Store<S>::ld(a + h + i)));
+    if (h >= 128) {
+      for (uint32_t i = lane; i < h; i += 128) {
+        float x[4], y[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          x[q] = Store<S>::ld(a + i + 32 * q);
+          y[q] = Store<S>::ld(a + h + i + 32 * q);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) Store<S>::st(c + i + 32 * q, f_op<FK>(x[q], y[q]));
+      }
+    } else {
+      for (uint32_t i = lane; i < h; i += 32)
+        Store<S>::st(c + i, f_op<FK>(Store<S>::ld(a + i), Store<S>::ld(a + h + i)));
+    }
     __syncwarp();
   }
 
   // Right child of the node of level k whose left child starts at leaf o.
   __device__ void g(int k, uint32_t o) const {
-    const S *a = lvl(k);
-    S *c = lvl(k - 1);
+    const S *__restrict__ a = lvl(k);
+    S *__restrict__ c = lvl(k - 1);
     const uint32_t h = 1u << (k - 1);
-    for (uint32_t i = lane; i < h; i += 32) {
-      uint32_t p = o + i;
-      uint32_t u = (beta[p >> 5] >> (p & 31)) & 1u;
-      Store<S>::st(c + i, g_op(Store<S>::ld(a + i), Store<S>::ld(a + h + i), u));
+    if (h >= 128) {
+      for (uint32_t i = lane; i < h; i += 128) {
+        float x[4], y[4];
+        uint32_t wd[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          x[q] = Store<S>::ld(a + i + 32 * q);
+          y[q] = Store<S>::ld(a + h + i + 32 * q);
+          wd[q] = beta[(o + i + 32 * q) >> 5];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          Store<S>::st(c + i + 32 * q, g_bit(x[q], y[q], wd[q], (o + i) & 31));
+      }
+    } else {
+      for (uint32_t i = lane; i < h; i += 32) {
+        uint32_t p = o + i;
+        Store<S>::st(c + i, g_bit(Store<S>::ld(a + i), Store<S>::ld(a + h + i), beta[p >> 5],
+                                  p & 31));
+      }
     }
     __syncwarp();
   }
@@ -175,22 +314,35 @@ struct Warp {
   }
 };
 
+// Words of shared memory before the LLR levels: beta, u_hat, mask, frozen
+// values (W each) and the two class-table halves (CW each), rounded up to 16 B.
+__host__ __device__ inline uint32_t bit_words(int t) {
+  const uint32_t W = t >= 5 ? (1u << (t - 5)) : 1u;
+  const uint32_t CW = t >= 9 ? (1u << (t - 9)) : 1u;
+  return (4 * W + 2 * CW + 3u) & ~3u;
+}
+
 template <typename S, int FK, bool SC>
 __global__ void __launch_bounds__(32) k_subtree(StParams p, bool in_is_llr) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int t = p.t;
   const uint32_t T = 1u << t;
   const uint32_t W = T >= 32 ? T / 32 : 1;
+  const uint32_t CW = t >= 9 ? (1u << (t - 9)) : 1u;
   const int lane = threadIdx.x;
   const size_t fr = blockIdx.x;
 
   Warp<S> w;
   w.lane = lane;
+  w.t = t;
   w.beta = reinterpret_cast<uint32_t *>(smraw);
   w.uh = w.beta + W;
   w.msk = w.beta + 2 * W;
   w.fvw = w.beta + 3 * W;
-  w.L = reinterpret_cast<S *>(w.beta + 4 * W);
+  uint32_t *ctab = w.beta + 4 * W;
+  w.cr0 = ctab;
+  w.cr1 = ctab + CW;
+  w.L = reinterpret_cast<S *>(w.beta + bit_words(t));
 
   const uint64_t ow = p.o >> 5;
   const uint32_t *fvf = p.fv + fr * p.w_stride + ow;
@@ -200,6 +352,8 @@ __global__ void __launch_bounds__(32) k_subtree(StParams p, bool in_is_llr) {
     w.beta[i] = 0u;
     w.uh[i] = 0u;
   }
+  if (SC && p.cls)
+    for (uint32_t i = lane; i < 2 * CW; i += 32) ctab[i] = p.cls[i];
   S *Lt = w.lvl(t);
   if (in_is_llr) {
     const float *src = reinterpret_cast<const float *>(p.in) + fr * p.in_stride;
@@ -210,35 +364,49 @@ __global__ void __launch_bounds__(32) k_subtree(StParams p, bool in_is_llr) {
   }
   __syncwarp();
 
-  int k = t;
-  uint32_t o = 0;
-  for (;;) {
-    for (;;) {                                   // descend
-      if (k == 0) {
-        w.leaf(o);
-        break;
-      }
-      if (SC) {
-        int cls = w.node_class(k, o);
-        if (cls == NODE_RATE0) {
-          w.rate0(k, o);
-          break;
+  if (SC && t < 5) {
+    // whole code shorter than a word: one register block with class checks
+    switch (t) {
+      case 1: w.template leafblock<1, FK, true>(0); break;
+      case 2: w.template leafblock<2, FK, true>(0); break;
+      case 3: w.template leafblock<3, FK, true>(0); break;
+      default: w.template leafblock<4, FK, true>(0); break;
+    }
+  } else {
+    int k = t;
+    uint32_t o = 0;
+    for (;;) {
+      for (;;) {                                 // descend
+        if (SC) {
+          const int cls = w.cls_tab(k, o);
+          if (cls == NODE_RATE0) {
+            w.rate0(k, o);
+            break;
+          }
+          if (cls == NODE_RATE1 && w.rate1(k, o)) break;
+          if (k == 5) {
+            w.template leafblock<5, FK, false>(o);
+            break;
+          }
+          if (k - 1 < 5 || w.cls_tab(k - 1, o) != NODE_RATE0) w.template f<FK>(k);
+        } else {
+          if (k == 0) {
+            w.leaf(o);
+            break;
+          }
+          w.template f<FK>(k);
         }
-        if (cls == NODE_RATE1 && w.rate1(k, o)) break;
-        if (w.node_class(k - 1, o) != NODE_RATE0) w.template f<FK>(k);
-      } else {
-        w.template f<FK>(k);
+        --k;
       }
-      --k;
+      while (k < t && ((o >> k) & 1u)) {         // ascend through right children
+        w.combine(k + 1, o - (1u << k));
+        o -= 1u << k;
+        ++k;
+      }
+      if (k == t) break;
+      w.g(k + 1, o);                             // right sibling's LLRs
+      o += 1u << k;
     }
-    while (k < t && ((o >> k) & 1u)) {           // ascend through right children
-      w.combine(k + 1, o - (1u << k));
-      o -= 1u << k;
-      ++k;
-    }
-    if (k == t) break;
-    w.g(k + 1, o);                               // right sibling's LLRs
-    o += 1u << k;
   }
 
   uint32_t *xf = p.xhat + fr * p.w_stride + ow;
@@ -256,14 +424,15 @@ template <typename S, int FK, bool SC>
 cudaError_t launch_t(const SubtreeArgs &a, cudaStream_t s) {
   const uint32_t T = 1u << a.t;
   const uint32_t W = T >= 32 ? T / 32 : 1;
-  size_t smem = 4 * W * sizeof(uint32_t) + 2 * (size_t)T * sizeof(S);
+  (void)W;
+  size_t smem = bit_words(a.t) * sizeof(uint32_t) + 2 * (size_t)T * sizeof(S);
   auto kern = k_subtree<S, FK, SC>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
-  StParams p{a.in, a.in_stride, a.mask, a.fv, a.xhat, a.uhat, a.w_stride, a.o, a.t, a.r};
+  StParams p{a.in, a.in_stride, a.cls, a.mask, a.fv, a.xhat, a.uhat, a.w_stride, a.o, a.t, a.r};
   kern<<<a.nframes, 32, smem, s>>>(p, a.in_is_llr);
   return counted(cudaGetLastError(), 1);
 }

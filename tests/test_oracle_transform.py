@@ -237,3 +237,58 @@ def test_llr_maps():
     assert O.llr_bsc(y, 0.02).tolist() == [np.float32(c), -np.float32(c), -np.float32(c), np.float32(c)]
     yy = np.array([0.3, -1.7, 2.5])
     assert np.array_equal(O.llr_biawgn(yy, 0.5), (yy * 4.0).astype(np.float32))
+
+
+# ------------------------------------------------------------------ storage modes
+def test_store_fp32_equals_float_decoder():
+    rng = np.random.default_rng(123)
+    n = 10
+    N = 1 << n
+    fz = (rng.random(N) < 0.5).astype(np.uint8)
+    fv = (rng.integers(0, 2, N) * fz).astype(np.uint8)
+    L = rng.normal(0.5, 2.0, N).astype(np.float32)
+    for fk in ("minsum", "exact"):
+        u0, x0, l0 = O.sc_decode(L, fz, fv, fk, leaf=True)
+        u1, x1, l1 = O.sc_decode_store(L, fz, fv, fk, "fp32", leaf=True)
+        assert np.array_equal(x0, x1) and np.array_equal(u0, u1) and np.array_equal(l0, l1)
+
+
+def test_store_rounding_points_n2():
+    """N = 2 closed forms of the storage rounding: the g output is stored."""
+    _, _, lf = O.sc_decode_store(np.array([1024, 1025], np.float32), [0, 0], [0, 0],
+                                 "minsum", "fp16", leaf=True)
+    assert lf.tolist() == [1024.0, 2048.0]          # 2049 rounds to even half 2048
+    _, _, lf = O.sc_decode_store(np.array([60000, 60000], np.float32), [0, 0], [0, 0],
+                                 "minsum", "fp16", leaf=True)
+    assert lf.tolist() == [60000.0, 65504.0]        # saturated, not inf
+    _, _, lf = O.sc_decode_store(np.array([100, 100], np.float32), [0, 0], [0, 0],
+                                 "minsum", "int8", 1.0, leaf=True)
+    assert lf.tolist() == [100.0, 127.0]
+    _, _, lf = O.sc_decode_store(np.array([2.4, -3.6], np.float32), [0, 0], [0, 0],
+                                 "minsum", "int8", 4.0, leaf=True)
+    # inputs 9.6 -> 10, -14.4 -> -14; f = -10; u0 = 1 so g = -14 - 10 = -24
+    assert lf.tolist() == [-10.0, -24.0]
+
+
+@pytest.mark.parametrize("store", ["fp16", "int8"])
+def test_store_exact_when_nothing_rounds(store):
+    """Small-integer LLRs whose partial sums stay within range round nowhere,
+    so the reduced-storage decoder equals the float one bit for bit."""
+    rng = np.random.default_rng(7)
+    n = 6
+    N = 1 << n
+    for _ in range(50):
+        L = rng.integers(-1, 2, N).astype(np.float32)       # |sums| <= 64 < 127
+        fz = (rng.random(N) < 0.5).astype(np.uint8)
+        fv = (rng.integers(0, 2, N) * fz).astype(np.uint8)
+        u0, x0 = O.sc_decode(L, fz, fv, "minsum")
+        u1, x1 = O.sc_decode_store(L, fz, fv, "minsum", store, 1.0)
+        assert np.array_equal(x0, x1) and np.array_equal(u0, u1)
+
+
+def test_int8_scale_power_of_two():
+    L = np.full(1024, 3.4761, np.float32)
+    s = O.int8_scale(L, 8.0)
+    assert s == 2.0                  # log2(8 / 3.4761) = 1.20 -> 2^1
+    assert O.int8_scale(np.zeros(8, np.float32)) == 1.0
+    assert O.int8_scale(np.full(4, 0.01, np.float32), 8.0) == 1024.0
