@@ -70,7 +70,7 @@ const char *polar_last_error_string(void);
 /* Process-wide tuning knobs, by name.  Returns POLAR_ENOTFOUND for an
  * unknown key, POLAR_EINVAL for a value out of range.  Keys:
  *   "subtree_log2"  t, log2 of the leaves one CTA decodes in shared memory
- *                   (5..13; default 13); levels above t stream through HBM.
+ *                   (5..14; default 13); levels above t stream through HBM.
  *   "shortcuts"     1 = rate-0 / rate-1 node shortcuts (default), 0 = none.
  *   "graphs"        1 = replay batch launch sequences as CUDA graphs
  *                   (default), 0 = launch every kernel eagerly.
@@ -78,6 +78,9 @@ const char *polar_last_error_string(void);
  *                   after another, no shortcuts, no graphs; 0 (default).
  *   "profile"       1 = time every kernel group with CUDA events (eager
  *                   launches, see polar_profile_read); 0 (default).
+ *   "int8_target"   INT8 storage: the per-frame scale is the power of two
+ *                   2^rint(log2(target / mean|L|)) (mean in double over the
+ *                   frame's channel LLRs); 1..64, default 8.
  */
 int polar_config_set(const char *key, long value);
 int polar_config_get(const char *key, long *value);
@@ -202,6 +205,67 @@ typedef struct {
  * frozen set whose buffers are equally strided are decoded as one batch. */
 int polar_sc_decode_batch(int nframes, const polar_frame_desc *frames,
                           polar_fkind fkind, polar_prec prec, void *stream);
+
+/* ---------------------------------------------------------------- serving */
+
+/* Continuous-batching request server (the serving pattern around the SC
+ * decoder of Sec. 4; the paper itself decodes one frame at a time).
+ * Requests enter a bounded host queue; a scheduler thread launches the oldest
+ * pending request on a free decode slot (a non-blocking CUDA stream with its
+ * own scratch) as soon as a slot is free and the scratch budget allows, so
+ * requests that arrive while others run overlap with them on the device.
+ * The server never touches request buffers after reporting completion. */
+typedef struct polar_server polar_server;
+
+typedef struct {
+    int device;         /* CUDA device ordinal the server decodes on */
+    int max_inflight;   /* decode slots (CUDA streams), 1..256 */
+    int max_queue;      /* pending requests held before submit returns EBUSY */
+    size_t mem_budget;  /* bytes of decode scratch all slots may hold together */
+    polar_fkind fkind;
+    polar_prec prec;
+} polar_server_config;
+
+typedef struct {
+    const polar_frozen_set *fs;
+    int nframes;                  /* contiguous frames sharing fs, >= 1 */
+    const float *llr;             /* device [nframes][N], 16-byte aligned */
+    const uint32_t *frozen_vals;  /* device [nframes][N/32] */
+    uint32_t *xhat;               /* device [nframes][N/32] */
+    uint32_t *uhat;               /* device [nframes][N/32] or NULL */
+} polar_request;
+
+typedef struct {
+    int status;         /* POLAR_OK or a negative polar_status */
+    double queue_ms;    /* submit -> launch on a slot */
+    double latency_ms;  /* submit -> completion observed by the scheduler */
+} polar_result;
+
+/* Start a server (EINVAL: bad config or device; ECUDA: stream creation). */
+int polar_server_create(const polar_server_config *cfg, polar_server **out);
+
+/* Queue a request; *ticket identifies it.  EINVAL: bad request (checked on
+ * the host); EBUSY: the queue holds max_queue requests (admission refused,
+ * retry later).  The caller keeps every buffer alive until completion. */
+int polar_server_submit(polar_server *srv, const polar_request *req, uint64_t *ticket);
+
+/* POLAR_PENDING while the request runs; once done, its final status (OK or
+ * an error: ENOMEM when its scratch alone exceeds mem_budget, ECUDA on a
+ * failed launch) with *out filled, after which the ticket is forgotten.
+ * ENOTFOUND for an unknown or already reported ticket. */
+int polar_server_poll(polar_server *srv, uint64_t ticket, polar_result *out);
+
+/* As poll, but blocks up to timeout_ms; ETIMEDOUT if still pending. */
+int polar_server_wait(polar_server *srv, uint64_t ticket, double timeout_ms,
+                      polar_result *out);
+
+/* Counters since creation: requests launched, completed, refused with EBUSY,
+ * and the scratch bytes the slots hold.  Any pointer may be NULL. */
+int polar_server_stats(polar_server *srv, uint64_t *launched, uint64_t *completed,
+                       uint64_t *refused, size_t *scratch_bytes);
+
+/* Finish queued and running requests, then release streams and scratch. */
+void polar_server_destroy(polar_server *srv);
 
 /* ------------------------------------------------- decoding, no allocation */
 

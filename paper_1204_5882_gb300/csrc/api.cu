@@ -21,6 +21,7 @@ struct Config {
   std::atomic<long> graphs{1};
   std::atomic<long> plain{0};
   std::atomic<long> profile{0};
+  std::atomic<long> int8_target{8};
 };
 Config g_cfg;
 
@@ -156,10 +157,26 @@ struct Exec {
   const uint32_t *dclass;   // class table (shortcuts, t >= 5) or null
 };
 
+// Workspace: [int8 scales, F floats rounded up to 256 B][levels t..n-1].
+inline size_t scale_region(int nframes, int prec) {
+  return prec == POLAR_INT8 ? ((size_t)nframes * sizeof(float) + 255) & ~size_t(255) : 0;
+}
+
+inline float *scale_ptr(const Exec &x) {
+  return x.g->prec == POLAR_INT8 ? static_cast<float *>(x.ws) : nullptr;
+}
+
 inline void *level_ptr(const Exec &x, int k) {
   // levels t .. n-1 of all frames: level k at F * (2^k - 2^t) elements
   size_t off = (size_t)x.g->nframes * ((size_t(1) << k) - (size_t(1) << x.t));
-  return static_cast<char *>(x.ws) + off * storage_bytes(x.g->prec);
+  return static_cast<char *>(x.ws) + scale_region(x.g->nframes, x.g->prec) +
+         off * storage_bytes(x.g->prec);
+}
+
+inline size_t workspace_bytes(int n, int t, int nframes, int prec) {
+  size_t lv = n > t ? (size_t)nframes * ((size_t(1) << n) - (size_t(1) << t)) * storage_bytes(prec)
+                    : 0;
+  return scale_region(nframes, prec) + lv;
 }
 
 int run_ops(const Exec &x, cudaStream_t s, bool prof) {
@@ -168,6 +185,8 @@ int run_ops(const Exec &x, cudaStream_t s, bool prof) {
   const uint64_t N = uint64_t(1) << n;
   const size_t W = N >= 32 ? N / 32 : 1;
   const double F = g.nframes, sb = (double)storage_bytes(g.prec);
+  float *scale = scale_ptr(x);
+  if (scale) CK(launch_int8_scale(g.llr, N, g.nframes, (double)g_cfg.int8_target.load(), scale, s));
   for (const Op &op : x.plan->ops) {
     switch (op.kind) {
       case OP_F:
@@ -182,9 +201,10 @@ int run_ops(const Exec &x, cudaStream_t s, bool prof) {
         ProfScope ps(prof, op.kind == OP_F ? 1 : 2,
                      F * (2.0 * h * inb + h * sb + (op.kind == OP_G ? h / 8.0 : 0.0)), s);
         if (op.kind == OP_F) {
-          CK(launch_stream_f(g.prec, g.fkind, in, ins, top, out, h, h, g.nframes, s));
+          CK(launch_stream_f(g.prec, g.fkind, in, ins, top, out, h, h, g.nframes, scale, s));
         } else {
-          CK(launch_stream_g(g.prec, in, ins, top, out, h, h, g.xhat, W, op.o, g.nframes, s));
+          CK(launch_stream_g(g.prec, in, ins, top, out, h, h, g.xhat, W, op.o, g.nframes, scale,
+                             s));
         }
         break;
       }
@@ -195,6 +215,7 @@ int run_ops(const Exec &x, cudaStream_t s, bool prof) {
         a.in_stride = a.in_is_llr ? N : (size_t(1) << t);
         a.mask = x.dmask;
         a.cls = x.dclass ? x.dclass + (op.o >> t) * 2 * class_words(t) : nullptr;
+        a.scale = scale;
         a.fv = g.fv;
         a.xhat = g.xhat;
         a.uhat = g.uhat;
@@ -236,13 +257,28 @@ int current_device(int *dev) {
   return POLAR_OK;
 }
 
-int decode_group(const Group &g, cudaStream_t s) {
+struct Opts {
+  bool plain, shortcuts, graphs, profile;
+  int subtree_log2;
+};
+
+Opts current_opts() {
+  Opts o;
+  o.plain = g_cfg.plain.load() != 0;
+  o.shortcuts = !o.plain && g_cfg.shortcuts.load() != 0;
+  o.graphs = !o.plain && g_cfg.graphs.load() != 0;
+  o.profile = g_cfg.profile.load() != 0;
+  o.subtree_log2 = (int)g_cfg.subtree_log2.load();
+  return o;
+}
+
+int decode_group(const Group &g, cudaStream_t s, const Opts &opt) {
   polar_frozen_set *fs = g.fs;
   const int n = (int)fs->log2n;
-  const bool plain = g_cfg.plain.load() != 0;
-  const bool shortcuts = !plain && g_cfg.shortcuts.load() != 0;
-  const bool graphs = !plain && g_cfg.graphs.load() != 0;
-  const int t = std::min<int>(n, (int)g_cfg.subtree_log2.load());
+  const bool plain = opt.plain;
+  const bool shortcuts = opt.shortcuts;
+  const bool graphs = opt.graphs;
+  const int t = std::min<int>(n, opt.subtree_log2);
   int dev = 0;
   int rc = current_device(&dev);
   if (rc) return rc;
@@ -256,8 +292,7 @@ int decode_group(const Group &g, cudaStream_t s) {
     if (!dclass) return e == cudaErrorMemoryAllocation ? POLAR_ENOMEM : cuda_fail(e);
   }
   const int F = plain ? 1 : g.nframes;
-  size_t ws_bytes = n > t ? (size_t)F * ((size_t(1) << n) - (size_t(1) << t)) * storage_bytes(g.prec)
-                          : 0;
+  size_t ws_bytes = workspace_bytes(n, t, F, g.prec);
   void *ws = nullptr;
   if (ws_bytes) {
     rc = get_workspace(dev, s, ws_bytes, &ws);
@@ -274,13 +309,13 @@ int decode_group(const Group &g, cudaStream_t s) {
       one.xhat = g.xhat + (size_t)f * W;
       one.uhat = g.uhat ? g.uhat + (size_t)f * W : nullptr;
       Exec x{plan.get(), &one, dmask, ws, n, t, dclass};
-      rc = run_ops(x, s, g_cfg.profile.load() != 0);
+      rc = run_ops(x, s, opt.profile);
       if (rc) return rc;
     }
     return POLAR_OK;
   }
   Exec x{plan.get(), &g, dmask, ws, n, t, dclass};
-  const bool prof = g_cfg.profile.load() != 0;
+  const bool prof = opt.profile;
   bool use_graph = graphs && !prof && s != nullptr;
   if (use_graph) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -335,7 +370,7 @@ int decode_group(const Group &g, cudaStream_t s) {
 int check_group(const Group &g) {
   if (!g.fs || g.nframes < 1 || !g.llr || !g.fv || !g.xhat) return POLAR_EINVAL;
   if (g.fkind != POLAR_F_MINSUM && g.fkind != POLAR_F_EXACT) return POLAR_EINVAL;
-  if (g.prec != POLAR_FP32 && g.prec != POLAR_FP16) return POLAR_EINVAL;
+  if (g.prec != POLAR_FP32 && g.prec != POLAR_FP16 && g.prec != POLAR_INT8) return POLAR_EINVAL;
   if (!aligned(g.llr, 16) || !aligned(g.fv, 4) || !aligned(g.xhat, 4)) return POLAR_EINVAL;
   if (g.uhat && !aligned(g.uhat, 4)) return POLAR_EINVAL;
   return POLAR_OK;
@@ -350,8 +385,7 @@ size_t level_scratch_bytes(const polar_frozen_set *fs, int nframes, int prec, in
   const int n = (int)fs->log2n;
   const int t = std::min<int>(n, (int)g_cfg.subtree_log2.load());
   if (t_out) *t_out = t;
-  if (n <= t) return 0;
-  return (size_t)nframes * ((size_t(1) << n) - (size_t(1) << t)) * storage_bytes(prec);
+  return workspace_bytes(n, t, nframes, prec);
 }
 
 // One batch decoded with launches only: the caller supplies the device mask
@@ -377,6 +411,33 @@ int decode_with_scratch(const polar_frozen_set *fs_c, int nframes, const float *
 }
 
 void set_last_error(const char *msg) { g_last_error = msg; }
+
+// Eager decode (no graphs, no plain mode) for callers that launch many
+// unrelated small batches, such as the request server.
+int decode_eager(const polar_frozen_set *fs, int nframes, const float *llr, const uint32_t *fv,
+                 uint32_t *xhat, uint32_t *uhat, int fkind, int prec, cudaStream_t s) {
+  Group g{const_cast<polar_frozen_set *>(fs), nframes, llr, fv, xhat, uhat, fkind, prec};
+  int rc = check_group(g);
+  if (rc) return rc;
+  Opts o = current_opts();
+  o.plain = false;
+  o.graphs = false;
+  o.profile = false;
+  o.shortcuts = g_cfg.shortcuts.load() != 0;
+  return decode_group(g, s, o);
+}
+
+void release_stream_workspace(int dev, cudaStream_t s) {
+  std::lock_guard<std::mutex> g(g_ws_mu);
+  auto it = g_ws.find({dev, s});
+  if (it == g_ws.end()) return;
+  if (it->second.ptr) cudaFree(it->second.ptr);
+  g_ws.erase(it);
+}
+
+size_t decode_scratch_bytes(const polar_frozen_set *fs, int nframes, int prec) {
+  return level_scratch_bytes(fs, nframes, prec, nullptr);
+}
 
 }  // namespace polar
 
@@ -412,6 +473,9 @@ int polar_config_set(const char *key, long value) {
     g_cfg.plain = value ? 1 : 0;
   } else if (!strcmp(key, "profile")) {
     g_cfg.profile = value ? 1 : 0;
+  } else if (!strcmp(key, "int8_target")) {
+    if (value < 1 || value > 64) return POLAR_EINVAL;
+    g_cfg.int8_target = value;
   } else {
     return POLAR_ENOTFOUND;
   }
@@ -425,6 +489,7 @@ int polar_config_get(const char *key, long *value) {
   else if (!strcmp(key, "graphs")) *value = g_cfg.graphs;
   else if (!strcmp(key, "plain")) *value = g_cfg.plain;
   else if (!strcmp(key, "profile")) *value = g_cfg.profile;
+  else if (!strcmp(key, "int8_target")) *value = g_cfg.int8_target;
   else return POLAR_ENOTFOUND;
   return POLAR_OK;
 }
@@ -554,7 +619,7 @@ int polar_sc_decode_many(const polar_frozen_set *fs, int nframes, const float *l
           uhat_dev, (int)fkind, (int)prec};
   int rc = check_group(g);
   if (rc) return rc;
-  return decode_group(g, static_cast<cudaStream_t>(stream));
+  return decode_group(g, static_cast<cudaStream_t>(stream), current_opts());
 }
 
 int polar_sc_decode(const polar_frozen_set *fs, const float *llr_dev,
@@ -590,7 +655,7 @@ int polar_sc_decode_batch(int nframes, const polar_frame_desc *frames, polar_fki
     }
     Group g{const_cast<polar_frozen_set *>(a.fs), j - i, a.llr, a.frozen_vals, a.xhat, a.uhat,
             (int)fkind, (int)prec};
-    int rc = decode_group(g, static_cast<cudaStream_t>(stream));
+    int rc = decode_group(g, static_cast<cudaStream_t>(stream), current_opts());
     if (rc) return rc;
     i = j;
   }

@@ -68,6 +68,30 @@ struct Store<int8_t> {
   }
 };
 
+// Value as it would be after a store to S (storage rounding / saturation);
+// used for levels that stay in registers and for channel LLRs on entry.
+template <typename S>
+__device__ __forceinline__ float rnd(float v);
+template <>
+__device__ __forceinline__ float rnd<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float rnd<__half>(float v) {
+  return __half2float(__float2half_rn(fminf(fmaxf(v, -65504.0f), 65504.0f)));
+}
+template <>
+__device__ __forceinline__ float rnd<int8_t>(float v) {
+  return fminf(fmaxf(rintf(v), -127.0f), 127.0f);
+}
+
+// f on stored values.  int8 values are L * s (s a per-frame power of two):
+// min-sum commutes with that scale exactly; exact f is evaluated on L.
+template <typename S, int FK>
+__device__ __forceinline__ float f_st(float a, float b, float s) {
+  if (FK == 0) return f_minsum(a, b);
+  if (sizeof(S) == 1) return s * f_exact(a / s, b / s);
+  return f_exact(a, b);
+}
+
 // ---------------------------------------------------------------- bits
 // x = u F^{(x)k} on the low 2^k bits of a word (k <= 5): for h = 1, 2, ...,
 // the low half of every block of 2h bits is XORed with its high half.

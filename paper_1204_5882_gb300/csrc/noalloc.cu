@@ -52,7 +52,7 @@ extern "C" int polar_sc_decode_many_noalloc(const polar_frozen_set *fs, int nfra
                                             uint32_t *xhat_dev, uint32_t *uhat_dev,
                                             polar_fkind fkind, polar_prec prec, void *stream) {
   if (!fs || nframes < 1 || !llr_dev || !frozen_vals_dev || !xhat_dev) return POLAR_EINVAL;
-  if (prec != POLAR_FP32 && prec != POLAR_FP16) return POLAR_EINVAL;
+  if (prec != POLAR_FP32 && prec != POLAR_FP16 && prec != POLAR_INT8) return POLAR_EINVAL;
   polar_frozen_set *fsm = const_cast<polar_frozen_set *>(fs);
   const size_t mask_bytes = ((fs->mask.size() * sizeof(uint32_t)) + 255) & ~size_t(255);
   int t = 0;

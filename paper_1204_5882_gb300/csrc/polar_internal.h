@@ -93,19 +93,25 @@ cudaError_t launch_cascade(uint32_t *xhat, size_t stride_w, int k_unit, uint64_t
                            int r, int nframes, cudaStream_t s);
 
 // Streamed f / g for levels above the subtree size (templated on storage).
+// Level-n inputs (in_is_llr) are the float channel LLRs; they are scaled
+// (int8) and rounded to the storage format on load.
 cudaError_t launch_stream_f(int prec, int fkind, const void *in, size_t in_stride,
                             bool in_is_llr, void *out, size_t out_stride, uint64_t h,
-                            int nframes, cudaStream_t s);
+                            int nframes, const float *scale, cudaStream_t s);
 cudaError_t launch_stream_g(int prec, const void *in, size_t in_stride, bool in_is_llr,
                             void *out, size_t out_stride, uint64_t h,
                             const uint32_t *xhat, size_t xhat_stride_w, uint64_t o,
-                            int nframes, cudaStream_t s);
+                            int nframes, const float *scale, cudaStream_t s);
+// Per-frame int8 scale 2^round(log2(target / mean|L|)) (1 if all L = 0).
+cudaError_t launch_int8_scale(const float *llr, size_t n, int nframes, double target,
+                              float *scale, cudaStream_t s);
 
 struct SubtreeArgs {
   const void *in;        // level-t LLRs of every frame (or the channel LLRs)
   size_t in_stride;      // elements between frames
   bool in_is_llr;        // in is the float channel LLR array (level n == t)
   const uint32_t *cls;   // device class table of this subtree (levels 5..t) or null
+  const float *scale;    // per-frame int8 scale (null = 1)
   const uint32_t *mask;  // device frozen mask (whole code)
   const uint32_t *fv;
   uint32_t *xhat;
@@ -131,6 +137,10 @@ int decode_with_scratch(const polar_frozen_set *fs, int nframes, const float *ll
                         size_t scratch_bytes, cudaStream_t s);
 bool shortcuts_enabled();
 void set_last_error(const char *msg);
+int decode_eager(const polar_frozen_set *fs, int nframes, const float *llr, const uint32_t *fv,
+                 uint32_t *xhat, uint32_t *uhat, int fkind, int prec, cudaStream_t s);
+size_t decode_scratch_bytes(const polar_frozen_set *fs, int nframes, int prec);
+void release_stream_workspace(int dev, cudaStream_t s);
 
 // Kernels launched by this library (graph replays included).
 extern std::atomic<uint64_t> g_kernel_launches;

@@ -186,13 +186,21 @@ cudaError_t launch_cascade(uint32_t *xhat, size_t stride_w, int k_unit, uint64_t
 // ---------------------------------------------------------------- stream f / g
 // Level k -> k-1 for every frame: out[j] = f(in[j], in[j+h]) or
 // g(in[j], in[j+h], beta[o+j]), j < h.  grid.y = frame; each thread handles
-// 4 consecutive j per step.
+// 4 consecutive j per step.  When the input is the float channel LLR array
+// and the storage is not float, inputs are scaled (int8) and rounded on load.
+template <typename Tin, typename Tout>
+__device__ __forceinline__ float load_in(const Tin *p, float sc) {
+  if constexpr (sizeof(Tin) == 4 && sizeof(Tout) != 4) return rnd<Tout>(*p * sc);
+  return Store<Tin>::ld(p);
+}
+
 template <typename Tin, typename Tout, int FK>
 __global__ void k_stream_f(const Tin *__restrict__ in, size_t in_stride, Tout *__restrict__ out,
-                           size_t out_stride, uint64_t h) {
+                           size_t out_stride, uint64_t h, const float *__restrict__ scale) {
   const Tin *a = in + blockIdx.y * in_stride;
   const Tin *b = a + h;
   Tout *o = out + blockIdx.y * out_stride;
+  const float sc = scale ? scale[blockIdx.y] : 1.0f;
   const uint64_t h4 = h >> 2;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < h4;
        i += (uint64_t)gridDim.x * blockDim.x) {
@@ -209,7 +217,8 @@ __global__ void k_stream_f(const Tin *__restrict__ in, size_t in_stride, Tout *_
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         uint64_t j = 4 * i + c;
-        Store<Tout>::st(o + j, f_op<FK>(Store<Tin>::ld(a + j), Store<Tin>::ld(b + j)));
+        Store<Tout>::st(o + j, f_st<Tout, FK>(load_in<Tin, Tout>(a + j, sc),
+                                              load_in<Tin, Tout>(b + j, sc), sc));
       }
     }
   }
@@ -218,11 +227,12 @@ __global__ void k_stream_f(const Tin *__restrict__ in, size_t in_stride, Tout *_
 template <typename Tin, typename Tout>
 __global__ void k_stream_g(const Tin *__restrict__ in, size_t in_stride, Tout *__restrict__ out,
                            size_t out_stride, uint64_t h, const uint32_t *__restrict__ xhat,
-                           size_t x_stride, uint64_t o_bits) {
+                           size_t x_stride, uint64_t o_bits, const float *__restrict__ scale) {
   const Tin *a = in + blockIdx.y * in_stride;
   const Tin *b = a + h;
   Tout *o = out + blockIdx.y * out_stride;
   const uint32_t *beta = xhat + blockIdx.y * x_stride + (o_bits >> 5);
+  const float sc = scale ? scale[blockIdx.y] : 1.0f;
   const uint64_t h4 = h >> 2;
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < h4;
        i += (uint64_t)gridDim.x * blockDim.x) {
@@ -240,8 +250,8 @@ __global__ void k_stream_g(const Tin *__restrict__ in, size_t in_stride, Tout *_
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         uint64_t j = 4 * i + c;
-        Store<Tout>::st(o + j,
-                        g_op(Store<Tin>::ld(a + j), Store<Tin>::ld(b + j), (bits >> c) & 1u));
+        Store<Tout>::st(o + j, g_op(load_in<Tin, Tout>(a + j, sc), load_in<Tin, Tout>(b + j, sc),
+                                    (bits >> c) & 1u));
       }
     }
   }
@@ -260,20 +270,22 @@ static dim3 stream_grid(uint64_t h, int nframes) {
 template <typename T>
 static cudaError_t stream_f_t(int fkind, const void *in, size_t in_stride, bool in_is_llr,
                               void *out, size_t out_stride, uint64_t h, int nframes,
-                              cudaStream_t s) {
+                              const float *scale, cudaStream_t s) {
   dim3 g = stream_grid(h, nframes);
   if (in_is_llr) {
     if (fkind == 0)
       k_stream_f<float, T, 0><<<g, 256, 0, s>>>((const float *)in, in_stride, (T *)out,
-                                                out_stride, h);
+                                                out_stride, h, scale);
     else
       k_stream_f<float, T, 1><<<g, 256, 0, s>>>((const float *)in, in_stride, (T *)out,
-                                                out_stride, h);
+                                                out_stride, h, scale);
   } else {
     if (fkind == 0)
-      k_stream_f<T, T, 0><<<g, 256, 0, s>>>((const T *)in, in_stride, (T *)out, out_stride, h);
+      k_stream_f<T, T, 0><<<g, 256, 0, s>>>((const T *)in, in_stride, (T *)out, out_stride, h,
+                                            scale);
     else
-      k_stream_f<T, T, 1><<<g, 256, 0, s>>>((const T *)in, in_stride, (T *)out, out_stride, h);
+      k_stream_f<T, T, 1><<<g, 256, 0, s>>>((const T *)in, in_stride, (T *)out, out_stride, h,
+                                            scale);
   }
   return counted(cudaGetLastError(), 1);
 }
@@ -281,14 +293,48 @@ static cudaError_t stream_f_t(int fkind, const void *in, size_t in_stride, bool 
 template <typename T>
 static cudaError_t stream_g_t(const void *in, size_t in_stride, bool in_is_llr, void *out,
                               size_t out_stride, uint64_t h, const uint32_t *xhat,
-                              size_t xs, uint64_t o, int nframes, cudaStream_t s) {
+                              size_t xs, uint64_t o, int nframes, const float *scale,
+                              cudaStream_t s) {
   dim3 g = stream_grid(h, nframes);
   if (in_is_llr)
     k_stream_g<float, T><<<g, 256, 0, s>>>((const float *)in, in_stride, (T *)out, out_stride, h,
-                                           xhat, xs, o);
+                                           xhat, xs, o, scale);
   else
     k_stream_g<T, T><<<g, 256, 0, s>>>((const T *)in, in_stride, (T *)out, out_stride, h, xhat,
-                                       xs, o);
+                                       xs, o, scale);
+  return counted(cudaGetLastError(), 1);
+}
+
+// ---------------------------------------------------------------- int8 scale
+// One CTA per frame: mean |L| in double (fixed reduction tree), then
+// s = 2^rint(log2(target / mean)), clamped to 2^+-100; s = 1 if every L = 0.
+__global__ void k_int8_scale(const float *__restrict__ llr, size_t n, double target,
+                             float *__restrict__ scale) {
+  __shared__ double part[256];
+  const float *p = llr + blockIdx.x * n;
+  double acc = 0.0;
+  for (size_t i = threadIdx.x; i < n; i += blockDim.x) acc += fabs((double)p[i]);
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double tot = part[0];
+    float sc = 1.0f;
+    if (tot > 0.0) {
+      double e = rint(log2(target / (tot / (double)n)));
+      e = fmin(fmax(e, -100.0), 100.0);
+      sc = (float)ldexp(1.0, (int)e);
+    }
+    scale[blockIdx.x] = sc;
+  }
+}
+
+cudaError_t launch_int8_scale(const float *llr, size_t n, int nframes, double target,
+                              float *scale, cudaStream_t s) {
+  k_int8_scale<<<nframes, 256, 0, s>>>(llr, n, target, scale);
   return counted(cudaGetLastError(), 1);
 }
 
@@ -298,20 +344,29 @@ size_t storage_bytes(int prec) { return prec == POLAR_FP32 ? 4 : (prec == POLAR_
 
 cudaError_t launch_stream_f(int prec, int fkind, const void *in, size_t in_stride,
                             bool in_is_llr, void *out, size_t out_stride, uint64_t h,
-                            int nframes, cudaStream_t s) {
+                            int nframes, const float *scale, cudaStream_t s) {
   if (prec == POLAR_FP16)
-    return stream_f_t<__half>(fkind, in, in_stride, in_is_llr, out, out_stride, h, nframes, s);
-  return stream_f_t<float>(fkind, in, in_stride, in_is_llr, out, out_stride, h, nframes, s);
+    return stream_f_t<__half>(fkind, in, in_stride, in_is_llr, out, out_stride, h, nframes,
+                              scale, s);
+  if (prec == POLAR_INT8)
+    return stream_f_t<int8_t>(fkind, in, in_stride, in_is_llr, out, out_stride, h, nframes,
+                              scale, s);
+  return stream_f_t<float>(fkind, in, in_stride, in_is_llr, out, out_stride, h, nframes, scale,
+                           s);
 }
 
 cudaError_t launch_stream_g(int prec, const void *in, size_t in_stride, bool in_is_llr,
                             void *out, size_t out_stride, uint64_t h, const uint32_t *xhat,
-                            size_t xhat_stride_w, uint64_t o, int nframes, cudaStream_t s) {
+                            size_t xhat_stride_w, uint64_t o, int nframes, const float *scale,
+                            cudaStream_t s) {
   if (prec == POLAR_FP16)
     return stream_g_t<__half>(in, in_stride, in_is_llr, out, out_stride, h, xhat, xhat_stride_w,
-                              o, nframes, s);
+                              o, nframes, scale, s);
+  if (prec == POLAR_INT8)
+    return stream_g_t<int8_t>(in, in_stride, in_is_llr, out, out_stride, h, xhat, xhat_stride_w,
+                              o, nframes, scale, s);
   return stream_g_t<float>(in, in_stride, in_is_llr, out, out_stride, h, xhat, xhat_stride_w, o,
-                           nframes, s);
+                           nframes, scale, s);
 }
 
 }  // namespace polar

@@ -33,6 +33,7 @@ struct StParams {
   const void *in;
   size_t in_stride;
   const uint32_t *cls;   // class table of this subtree (levels 5..t), or null
+  const float *scale;    // per-frame int8 scale, or null
   const uint32_t *mask;
   const uint32_t *fv;
   uint32_t *xhat;
@@ -43,47 +44,55 @@ struct StParams {
   int r;
 };
 
-// Value as it would be after a store to S (storage rounding / saturation),
-// so that register-resident levels behave like stored ones.
-template <typename S>
-__device__ __forceinline__ float rnd(float v);
-template <>
-__device__ __forceinline__ float rnd<float>(float v) { return v; }
-template <>
-__device__ __forceinline__ float rnd<__half>(float v) {
-  return __half2float(__float2half_rn(fminf(fmaxf(v, -65504.0f), 65504.0f)));
-}
-
 // g with the partial sum taken from bit j of a word: b + a or b - a (the
 // latter as b + (-a), which IEEE addition makes identical).
 __device__ __forceinline__ float g_bit(float a, float b, uint32_t word, int j) {
   return b + __uint_as_float(__float_as_uint(a) ^ ((word << (31 - j)) & 0x80000000u));
 }
 
+// Rate-1 test of a node held in registers: true (and the sign word in *b)
+// when no input is +-0; min and OR trees keep the dependency depth at K.
+template <int K>
+__device__ __forceinline__ bool signs_if_nonzero(const float (&a)[1 << K], uint32_t *b) {
+  constexpr int N = 1 << K;
+  float m[N];
+  uint32_t v[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    m[j] = fabsf(a[j]);
+    v[j] = (__float_as_uint(a[j]) >> 31) << j;
+  }
+#pragma unroll
+  for (int w = N / 2; w >= 1; w /= 2) {
+#pragma unroll
+    for (int j = 0; j < w; ++j) {
+      m[j] = fminf(m[j], m[j + w]);
+      v[j] |= v[j + w];
+    }
+  }
+  *b = v[0];
+  return m[0] > 0.0f;
+}
+
 // SC over a node of 2^K leaves held in registers: returns beta (2^K bits)
 // and u_hat in `u`.  frz / fv are the node's mask and frozen values in the
 // low 2^K bits.  CHECK: test the node itself for rate 0 / rate 1 first.
+// Nodes of up to 4 leaves take the generic path without class branches.
 template <int K, int FK, bool CHECK, typename S>
 struct Dec {
   static constexpr int N = 1 << K, H = N / 2;
   static __device__ __forceinline__ uint32_t run(const float (&a)[N], uint32_t frz, uint32_t fv,
-                                                 uint32_t &u) {
+                                                 uint32_t &u, float sc) {
     constexpr uint32_t M = (N == 32) ? 0xFFFFFFFFu : ((1u << N) - 1u);
     constexpr uint32_t MH = (1u << H) - 1u;
-    if (CHECK) {
+    if (CHECK && K >= 3) {
       if (frz == M) {
         u = fv;
         return encode_word(fv, K);
       }
       if (frz == 0u) {
-        float mn = fabsf(a[0]);
-        uint32_t b = __float_as_uint(a[0]) >> 31;
-#pragma unroll
-        for (int j = 1; j < N; ++j) {
-          mn = fminf(mn, fabsf(a[j]));
-          b |= (__float_as_uint(a[j]) >> 31) << j;
-        }
-        if (mn > 0.0f) {           // no zero input: signs are the decisions
+        uint32_t b;
+        if (signs_if_nonzero<K>(a, &b)) {   // no zero input: signs are the decisions
           u = encode_word(b, K);
           return b;
         }
@@ -92,18 +101,18 @@ struct Dec {
     float l[H];
     uint32_t uL, bL;
     const uint32_t fzL = frz & MH, fvL = fv & MH;
-    if (fzL == MH) {               // rate-0 left child: its f is never needed
+    if (K >= 3 && fzL == MH) {     // rate-0 left child: its f is never needed
       uL = fvL;
       bL = encode_word(fvL, K - 1);
     } else {
 #pragma unroll
-      for (int j = 0; j < H; ++j) l[j] = rnd<S>(f_op<FK>(a[j], a[j + H]));
-      bL = Dec<K - 1, FK, true, S>::run(l, fzL, fvL, uL);
+      for (int j = 0; j < H; ++j) l[j] = rnd<S>(f_st<S, FK>(a[j], a[j + H], sc));
+      bL = Dec<K - 1, FK, true, S>::run(l, fzL, fvL, uL, sc);
     }
 #pragma unroll
     for (int j = 0; j < H; ++j) l[j] = rnd<S>(g_bit(a[j], a[j + H], bL, j));
     uint32_t uR;
-    const uint32_t bR = Dec<K - 1, FK, true, S>::run(l, frz >> H, fv >> H, uR);
+    const uint32_t bR = Dec<K - 1, FK, true, S>::run(l, frz >> H, fv >> H, uR, sc);
     u = uL | (uR << H);
     return (bL ^ bR) | (bR << H);
   }
@@ -112,7 +121,7 @@ struct Dec {
 template <int FK, bool CHECK, typename S>
 struct Dec<0, FK, CHECK, S> {
   static __device__ __forceinline__ uint32_t run(const float (&a)[1], uint32_t frz, uint32_t fv,
-                                                 uint32_t &u) {
+                                                 uint32_t &u, float) {
     u = (frz & 1u) ? (fv & 1u) : (a[0] < 0.0f ? 1u : 0u);
     return u;
   }
@@ -124,6 +133,7 @@ struct Warp {
   uint32_t *beta, *uh, *msk, *fvw;
   const uint32_t *cr0, *cr1;   // class table: bit 2^(t-k) + (o >> k) for level k >= 5
   int lane, t;
+  float sc;                    // int8 per-frame scale (1 otherwise)
 
   __device__ __forceinline__ S *lvl(int k) const { return L + (1u << k); }
 
@@ -140,12 +150,24 @@ struct Warp {
     constexpr int N = 1 << K;
     const S *src = lvl(K);
     float a[N];
+    if constexpr (sizeof(S) == 4 && N >= 4) {     // level K starts 16-byte aligned
 #pragma unroll
-    for (int j = 0; j < N; ++j) a[j] = Store<S>::ld(src + j);
+      for (int j = 0; j < N; j += 4) {
+        float4 q = *reinterpret_cast<const float4 *>(src + j);
+        a[j] = q.x;
+        a[j + 1] = q.y;
+        a[j + 2] = q.z;
+        a[j + 3] = q.w;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < N; ++j) a[j] = Store<S>::ld(src + j);
+    }
     const uint32_t m = N == 32 ? 0xFFFFFFFFu : ((1u << N) - 1u);
     const uint32_t sh = o & 31;
     uint32_t u;
-    uint32_t b = Dec<K, FK, CHECK, S>::run(a, (msk[o >> 5] >> sh) & m, (fvw[o >> 5] >> sh) & m, u);
+    uint32_t b =
+        Dec<K, FK, CHECK, S>::run(a, (msk[o >> 5] >> sh) & m, (fvw[o >> 5] >> sh) & m, u, sc);
     if (lane == 0) {
       insert(beta, o, N, b);
       insert(uh, o, N, u);
@@ -261,11 +283,11 @@ struct Warp {
           y[q] = Store<S>::ld(a + h + i + 32 * q);
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) Store<S>::st(c + i + 32 * q, f_op<FK>(x[q], y[q]));
+        for (int q = 0; q < 4; ++q) Store<S>::st(c + i + 32 * q, f_st<S, FK>(x[q], y[q], sc));
       }
     } else {
       for (uint32_t i = lane; i < h; i += 32)
-        Store<S>::st(c + i, f_op<FK>(Store<S>::ld(a + i), Store<S>::ld(a + h + i)));
+        Store<S>::st(c + i, f_st<S, FK>(Store<S>::ld(a + i), Store<S>::ld(a + h + i), sc));
     }
     __syncwarp();
   }
@@ -335,6 +357,7 @@ __global__ void __launch_bounds__(32) k_subtree(StParams p, bool in_is_llr) {
   Warp<S> w;
   w.lane = lane;
   w.t = t;
+  w.sc = p.scale ? p.scale[fr] : 1.0f;
   w.beta = reinterpret_cast<uint32_t *>(smraw);
   w.uh = w.beta + W;
   w.msk = w.beta + 2 * W;
@@ -357,7 +380,7 @@ __global__ void __launch_bounds__(32) k_subtree(StParams p, bool in_is_llr) {
   S *Lt = w.lvl(t);
   if (in_is_llr) {
     const float *src = reinterpret_cast<const float *>(p.in) + fr * p.in_stride;
-    for (uint32_t i = lane; i < T; i += 32) Store<S>::st(Lt + i, src[i]);
+    for (uint32_t i = lane; i < T; i += 32) Store<S>::st(Lt + i, src[i] * w.sc);
   } else {
     const S *src = reinterpret_cast<const S *>(p.in) + fr * p.in_stride;
     for (uint32_t i = lane; i < T; i += 32) Lt[i] = src[i];
@@ -432,7 +455,8 @@ cudaError_t launch_t(const SubtreeArgs &a, cudaStream_t s) {
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
-  StParams p{a.in, a.in_stride, a.cls, a.mask, a.fv, a.xhat, a.uhat, a.w_stride, a.o, a.t, a.r};
+  StParams p{a.in,   a.in_stride, a.cls,      a.scale, a.mask, a.fv,
+             a.xhat, a.uhat,      a.w_stride, a.o,     a.t,    a.r};
   kern<<<a.nframes, 32, smem, s>>>(p, a.in_is_llr);
   return counted(cudaGetLastError(), 1);
 }
@@ -448,6 +472,7 @@ cudaError_t launch_s(const SubtreeArgs &a, cudaStream_t s) {
 
 cudaError_t launch_subtree(const SubtreeArgs &a, cudaStream_t s) {
   if (a.prec == POLAR_FP16) return launch_s<__half>(a, s);
+  if (a.prec == POLAR_INT8) return launch_s<int8_t>(a, s);
   return launch_s<float>(a, s);
 }
 

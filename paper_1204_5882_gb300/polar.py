@@ -37,6 +37,20 @@ class PolarError(RuntimeError):
         self.status = status
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("device", C.c_int), ("max_inflight", C.c_int), ("max_queue", C.c_int),
+                ("mem_budget", C.c_size_t), ("fkind", C.c_int), ("prec", C.c_int)]
+
+
+class Request(C.Structure):
+    _fields_ = [("fs", C.c_void_p), ("nframes", C.c_int), ("llr", C.c_void_p),
+                ("frozen_vals", C.c_void_p), ("xhat", C.c_void_p), ("uhat", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int), ("queue_ms", C.c_double), ("latency_ms", C.c_double)]
+
+
 class FrameDesc(C.Structure):
     _fields_ = [("fs", C.c_void_p), ("llr", C.c_void_p), ("frozen_vals", C.c_void_p),
                 ("xhat", C.c_void_p), ("uhat", C.c_void_p)]
@@ -68,6 +82,13 @@ def _load():
         "polar_sc_decode_many": ([P, I, P, P, P, P, I, I, P], I),
         "polar_sc_decode_batch": ([I, C.POINTER(FrameDesc), I, I, P], I),
         "polar_sc_decode_many_noalloc": ([P, I, P, P, P, P, I, I, P], I),
+        "polar_server_create": ([C.POINTER(ServerConfig), C.POINTER(P)], I),
+        "polar_server_submit": ([P, C.POINTER(Request), C.POINTER(U64)], I),
+        "polar_server_poll": ([P, U64, C.POINTER(Result)], I),
+        "polar_server_wait": ([P, U64, D, C.POINTER(Result)], I),
+        "polar_server_stats": ([P, C.POINTER(U64), C.POINTER(U64), C.POINTER(U64),
+                                C.POINTER(SZ)], I),
+        "polar_server_destroy": ([P], None),
         "polar_static_scratch_bytes": ([], SZ),
     }
     for name, (args, res) in sig.items():
@@ -224,6 +245,68 @@ def polar_sc_decode_many_noalloc(fs: FrozenSet, nframes: int, llr, fval, xhat, u
     _check("polar_sc_decode_many_noalloc", _lib.polar_sc_decode_many_noalloc(
         fs.handle, int(nframes), _ptr(llr), _ptr(fval), _ptr(xhat), _ptr(uhat), FKIND[fkind],
         PREC[prec], _stream(stream)))
+
+
+# ------------------------------------------------------------------ serving
+class Server:
+    """Owner of a library request server (destroyed on close / collection)."""
+
+    def __init__(self, device=0, max_inflight=32, max_queue=4096, mem_budget=8 << 30,
+                 fkind="minsum", prec="fp32"):
+        cfg = ServerConfig(int(device), int(max_inflight), int(max_queue), int(mem_budget),
+                           FKIND[fkind], PREC[prec])
+        h = C.c_void_p()
+        _check("polar_server_create", _lib.polar_server_create(C.byref(cfg), C.byref(h)))
+        self.handle = h
+
+    def submit(self, fs, nframes, llr, fval, xhat, uhat=None):
+        """Ticket, or None when admission is refused (queue full)."""
+        req = Request(fs.handle.value, int(nframes), llr.data_ptr(), fval.data_ptr(),
+                      xhat.data_ptr(), uhat.data_ptr() if uhat is not None else None)
+        t = C.c_uint64()
+        rc = _lib.polar_server_submit(self.handle, C.byref(req), C.byref(t))
+        if rc == POLAR_EBUSY:
+            return None
+        _check("polar_server_submit", rc)
+        return t.value
+
+    def poll(self, ticket):
+        """None while pending, else (status, queue_ms, latency_ms)."""
+        r = Result()
+        rc = _lib.polar_server_poll(self.handle, int(ticket), C.byref(r))
+        if rc == POLAR_PENDING:
+            return None
+        if rc == POLAR_ENOTFOUND:
+            raise PolarError("polar_server_poll", rc)
+        return (r.status, r.queue_ms, r.latency_ms)
+
+    def wait(self, ticket, timeout_ms=60000.0):
+        r = Result()
+        rc = _lib.polar_server_wait(self.handle, int(ticket), float(timeout_ms), C.byref(r))
+        if rc == POLAR_ETIMEDOUT:
+            raise PolarError("polar_server_wait", rc)
+        if rc == POLAR_ENOTFOUND:
+            raise PolarError("polar_server_wait", rc)
+        return (r.status, r.queue_ms, r.latency_ms)
+
+    def stats(self):
+        a, b, c, d = C.c_uint64(), C.c_uint64(), C.c_uint64(), C.c_size_t()
+        _check("polar_server_stats", _lib.polar_server_stats(self.handle, C.byref(a),
+                                                             C.byref(b), C.byref(c), C.byref(d)))
+        return {"launched": a.value, "completed": b.value, "refused": c.value,
+                "scratch_bytes": d.value}
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.polar_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+def polar_server_create(**kw) -> Server:
+    return Server(**kw)
 
 
 def polar_static_scratch_bytes() -> int:

@@ -105,3 +105,14 @@ def test_frozen_set_from_mask_roundtrip(P):
     assert fs.K == 64 - bin(0xDEADBEEF).count("1")
     fs = P.polar_frozen_set_from_mask(3, np.array([0xFFFFFF0F], dtype=np.uint32))
     assert fs.mask()[0] == 0x0F and fs.K == 4
+
+
+def test_server_config_rejected_on_host(P):
+    import ctypes as C
+    h = C.c_void_p()
+    for cfg in (P.ServerConfig(0, 0, 16, 1 << 30, 0, 0), P.ServerConfig(0, 4, 0, 1 << 30, 0, 0),
+                P.ServerConfig(0, 4, 16, 1 << 30, 5, 0), P.ServerConfig(0, 4, 16, 1 << 30, 0, 7),
+                P.ServerConfig(-1, 4, 16, 1 << 30, 0, 0)):
+        assert P.lib().polar_server_create(C.byref(cfg), C.byref(h)) == P.POLAR_EINVAL
+    assert P.lib().polar_server_submit(None, None, None) == P.POLAR_EINVAL
+    assert P.lib().polar_server_poll(None, 1, None) == P.POLAR_EINVAL

@@ -244,3 +244,47 @@ def test_exact_f_fer_matches_float64_oracle(P):
     se = math.sqrt(max(pg * (1 - pg), 1.0 / T) / T + max(po * (1 - po), 1.0 / T) / T)
     assert 0.02 < po < 0.98, po
     assert abs(pg - po) <= 2 * se, (pg, po, se)
+
+
+# ------------------------------------------------------------------ reduced storage
+def check_store(P, n, kind, F, seed, prec, llr_kind="gauss"):
+    N = 1 << n
+    rng = np.random.default_rng(seed)
+    fz = random_code(rng, n, kind)
+    fs = P.polar_frozen_set_from_mask(n, S.pack_bits(fz))
+    if llr_kind == "gauss":
+        L = rng.normal(0.5, 2.0, (F, N)).astype(np.float32)
+    else:
+        L = (np.float32(2.5) * (1 - 2 * (rng.random((F, N)) < 0.1))).astype(np.float32)
+    fvb = (rng.integers(0, 2, (F, N)) * fz).astype(np.uint8)
+    fvw = np.stack([S.pack_bits(r) for r in fvb])
+    xh, uh = gpu_decode(P, fs, L, fvw, "minsum", prec)
+    for f in range(F):
+        sc = O.int8_scale(L[f], P.polar_config_get("int8_target")) if prec == "int8" else 1.0
+        ou, ox = O.sc_decode_store(L[f], fz, fvb[f], "minsum", prec, sc)
+        assert np.array_equal(S.unpack_bits(xh[f], N), ox), (n, kind, prec, f)
+        assert np.array_equal(S.unpack_bits(uh[f], N), ou), (n, kind, prec, f)
+
+
+@pytest.mark.parametrize("prec", ["fp16", "int8"])
+@pytest.mark.parametrize("t", [5, 9, 13])
+@pytest.mark.parametrize("n", [3, 5, 8, 12, 15])
+def test_reduced_storage_minsum_bitexact(P, prec, t, n):
+    """FP16 / INT8 storage: every stored LLR rounded (and saturated) exactly as
+    the oracle's storage model does, so min-sum decisions match bit for bit."""
+    P.polar_config_set("subtree_log2", t)
+    check_store(P, n, "polar", 3, 500 + n + t, prec, "gauss")
+    check_store(P, n, "random", 2, 600 + n + t, prec, "bsc")
+
+
+@pytest.mark.parametrize("prec", ["fp16", "int8"])
+def test_reduced_storage_workload_bitexact(P, prec):
+    w = S.WORKLOADS["bsc_p03_n20"]
+    fs, x, y, xh, uh = decode_workload_gpu(P, w, 0, 8, "minsum", prec)
+    ofz, _ = O.frozen_set(w.log2n, w.channel, w.param, w.rate)
+    for f in range(8):
+        L = O.llr_bsc(S.unpack_bits(y[f], w.N), w.param, 32)
+        fv = O.reveal(S.unpack_bits(x[f], w.N), ofz)
+        sc = O.int8_scale(L, P.polar_config_get("int8_target")) if prec == "int8" else 1.0
+        ou, ox = O.sc_decode_store(L, ofz, fv, "minsum", prec, sc)
+        assert np.array_equal(S.unpack_bits(xh[f], w.N), ox), f

@@ -1,0 +1,148 @@
+"""Request server (continuous batching) through the C ABI.
+
+Results decoded in a mix of concurrent requests of several lengths and codes
+equal the results of the same requests decoded alone (bit-exact, float32
+min-sum), and a sample equals the oracle; admission refusals, the memory
+budget and the bounded wait behave as declared.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_1204_5882_gb300 import synth as S  # noqa: E402
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1204_5882_gb300 import build
+    build.build()
+    from paper_1204_5882_gb300 import polar
+    return polar
+
+
+def make_requests(P, count, seed, sizes=(10, 12, 14, 16)):
+    rng = np.random.default_rng(seed)
+    codes = {}
+    reqs = []
+    for i in range(count):
+        n = int(rng.choice(sizes))
+        kind = int(rng.integers(0, 3))
+        if (n, kind) not in codes:
+            if kind == 0:
+                fz, _ = O.frozen_set(n, "bsc", 0.03, 0.6)
+            elif kind == 1:
+                fz, _ = O.frozen_set(n, "biawgn", 1.0, 0.4)
+            else:
+                fz = (rng.random(1 << n) < 0.5).astype(np.uint8)
+            codes[(n, kind)] = (fz, P.polar_frozen_set_from_mask(n, S.pack_bits(fz)))
+        fz, fs = codes[(n, kind)]
+        F = int(rng.integers(1, 3))
+        N = 1 << n
+        L = rng.normal(0.7, 2.0, (F, N)).astype(np.float32)
+        fvb = (rng.integers(0, 2, (F, N)) * fz).astype(np.uint8)
+        fvw = np.stack([S.pack_bits(r) for r in fvb])
+        reqs.append(dict(n=n, F=F, fz=fz, fs=fs, L=L, fvb=fvb,
+                         llr=torch.from_numpy(L).to(DEV),
+                         fv=torch.from_numpy(fvw.view(np.int32)).to(DEV)))
+    return reqs
+
+
+@pytest.mark.gpu
+def test_results_identical_alone_and_in_mix(P):
+    reqs = make_requests(P, 40, 11)
+    stream = torch.cuda.Stream()
+    alone = []
+    for r in reqs:                                   # one at a time, synchronously
+        xh = torch.zeros_like(r["fv"])
+        P.polar_sc_decode_many(r["fs"], r["F"], r["llr"], r["fv"], xh, None, "minsum", "fp32",
+                               stream)
+        stream.synchronize()
+        alone.append(xh.cpu())
+    srv = P.Server(max_inflight=16, max_queue=1024)
+    outs, tickets = [], []
+    for r in reqs:                                   # all at once: they overlap
+        xh = torch.full_like(r["fv"], -1)
+        outs.append(xh)
+        t = srv.submit(r["fs"], r["F"], r["llr"], r["fv"], xh)
+        assert t is not None
+        tickets.append(t)
+    for t in tickets:
+        st, q_ms, lat_ms = srv.wait(t, 60000.0)
+        assert st == P.POLAR_OK and lat_ms >= q_ms >= 0.0
+    stats = srv.stats()
+    srv.close()
+    assert stats["completed"] == len(reqs)
+    for r, a, b in zip(reqs, alone, outs):
+        assert torch.equal(a, b.cpu())
+    for r, b in list(zip(reqs, outs))[:6]:           # and the oracle agrees
+        got = b.cpu().numpy().view(np.uint32)
+        for f in range(r["F"]):
+            _, ox = O.sc_decode(r["L"][f], r["fz"], r["fvb"][f], "minsum")
+            assert np.array_equal(S.unpack_bits(got[f], 1 << r["n"]), ox)
+
+
+@pytest.mark.gpu
+def test_admission_refused_when_queue_full(P):
+    reqs = make_requests(P, 30, 12, sizes=(16,))
+    srv = P.Server(max_inflight=1, max_queue=2)
+    accepted, refused = [], 0
+    outs = []
+    for r in reqs:
+        xh = torch.zeros_like(r["fv"])
+        outs.append(xh)
+        t = srv.submit(r["fs"], r["F"], r["llr"], r["fv"], xh)
+        if t is None:
+            refused += 1
+        else:
+            accepted.append(t)
+    assert refused > 0 and accepted
+    for t in accepted:
+        assert srv.wait(t)[0] == P.POLAR_OK
+    assert srv.stats()["refused"] == refused
+    srv.close()
+
+
+@pytest.mark.gpu
+def test_memory_budget_serialises_and_rejects(P):
+    reqs = make_requests(P, 6, 13, sizes=(18,))
+    need = max((1 << 18) - (1 << 13), 0) * 4 * 2      # two frames of 2^18 in FP32
+    srv = P.Server(max_inflight=8, max_queue=64, mem_budget=need)
+    outs, tickets = [], []
+    for r in reqs:
+        xh = torch.zeros_like(r["fv"])
+        outs.append(xh)
+        tickets.append(srv.submit(r["fs"], r["F"], r["llr"], r["fv"], xh))
+    for t in tickets:
+        assert srv.wait(t)[0] == P.POLAR_OK
+    assert srv.stats()["scratch_bytes"] <= need
+    # a request whose scratch alone exceeds the budget fails with ENOMEM
+    big = make_requests(P, 1, 14, sizes=(20,))[0]
+    xh = torch.zeros_like(big["fv"])
+    t = srv.submit(big["fs"], big["F"], big["llr"], big["fv"], xh)
+    assert srv.wait(t)[0] == P.POLAR_ENOMEM
+    srv.close()
+
+
+@pytest.mark.gpu
+def test_bounded_wait_and_bad_tickets(P):
+    r = make_requests(P, 1, 15, sizes=(16,))[0]
+    srv = P.Server(max_inflight=2)
+    xh = torch.zeros_like(r["fv"])
+    t = srv.submit(r["fs"], r["F"], r["llr"], r["fv"], xh)
+    try:
+        st = srv.wait(t, 0.0)                        # may already be done
+    except P.PolarError as e:                        # still running: bounded wait expired
+        assert e.status == P.POLAR_ETIMEDOUT
+        st = srv.wait(t, 60000.0)
+    assert st[0] == P.POLAR_OK
+    with pytest.raises(P.PolarError):
+        srv.poll(t)                                  # reported once, then forgotten
+    with pytest.raises(P.PolarError):
+        srv.poll(987654321)
+    srv.close()
