@@ -85,7 +85,7 @@ struct Dec {
                                                  uint32_t &u, float sc) {
     constexpr uint32_t M = (N == 32) ? 0xFFFFFFFFu : ((1u << N) - 1u);
     constexpr uint32_t MH = (1u << H) - 1u;
-    if (CHECK && K >= 3) {
+    if (CHECK && K >= 5) {
       if (frz == M) {
         u = fv;
         return encode_word(fv, K);
@@ -145,7 +145,7 @@ struct Warp {
   }
 
   // Mixed node of 2^K leaves (K <= 5) at leaf o, decoded in registers.
-  template <int K, int FK, bool CHECK>
+  template <int K, int FK, bool CHECK, bool UH>
   __device__ void leafblock(uint32_t o) const {
     constexpr int N = 1 << K;
     const S *src = lvl(K);
@@ -170,7 +170,7 @@ struct Warp {
         Dec<K, FK, CHECK, S>::run(a, (msk[o >> 5] >> sh) & m, (fvw[o >> 5] >> sh) & m, u, sc);
     if (lane == 0) {
       insert(beta, o, N, b);
-      insert(uh, o, N, u);
+      if (UH) insert(uh, o, N, u);
     }
     __syncwarp();
   }
@@ -210,12 +210,13 @@ struct Warp {
     v[o >> 5] = (v[o >> 5] & ~m) | ((bits << (o & 31)) & m);
   }
 
+  template <bool UH = true>
   __device__ void rate0(int k, uint32_t o) const {
     if (k >= 5) {
       uint32_t w0 = o >> 5, nw = 1u << (k - 5);
       for (uint32_t i = lane; i < nw; i += 32) {
         uint32_t v = fvw[w0 + i];
-        uh[w0 + i] = v;
+        if (UH) uh[w0 + i] = v;
         beta[w0 + i] = encode_word(v, 5);
       }
       xword_encode(beta, w0, nw);
@@ -229,30 +230,57 @@ struct Warp {
     }
   }
 
-  // Rate-1 shortcut; false (nothing written) when some input is +-0.
+  // Rate-1 shortcut (k >= 5); false (nothing written) when some input is +-0.
+  // Each lane builds whole words of hard decisions (32 LLRs per word), so a
+  // node costs one pass over its LLRs and one vote.
+  template <bool UH>
   __device__ bool rate1(int k, uint32_t o) const {
     const S *Lk = lvl(k);
-    const uint32_t n = 1u << k;
+    const uint32_t w0 = o >> 5, nw = 1u << (k - 5);
+    if (nw == 1) {
+      const float v = Store<S>::ld(Lk + lane);
+      if (__any_sync(FULL, v == 0.0f)) return false;
+      const uint32_t b = __ballot_sync(FULL, v < 0.0f);
+      if (lane == 0) {
+        beta[w0] = b;
+        if (UH) uh[w0] = encode_word(b, 5);
+      }
+      __syncwarp();
+      return true;
+    }
     bool z = false;
-    for (uint32_t i = lane; i < n; i += 32) z |= (Store<S>::ld(Lk + i) == 0.0f);
-    if (__any_sync(FULL, z)) return false;
-    if (k >= 5) {
-      uint32_t w0 = o >> 5, nw = 1u << (k - 5);
-      for (uint32_t i = 0; i < nw; ++i) {
-        uint32_t b = __ballot_sync(FULL, Store<S>::ld(Lk + 32 * i + lane) < 0.0f);
-        if (lane == 0) {
-          beta[w0 + i] = b;
-          uh[w0 + i] = encode_word(b, 5);
+    uint32_t words[8];                   // nw <= 2^(t-5) <= 512: 16 words per lane at most
+#pragma unroll
+    for (int r = 0; r < 8; ++r) words[r] = 0u;
+    for (uint32_t i = lane, r = 0; i < nw; i += 32, ++r) {
+      uint32_t b = 0u;
+      const S *q = Lk + 32 * i;
+      if constexpr (sizeof(S) == 4) {   // level k >= 6 starts 16-byte aligned
+#pragma unroll
+        for (int j = 0; j < 32; j += 4) {
+          const float4 v = *reinterpret_cast<const float4 *>(q + j);
+          z |= (v.x == 0.0f) | (v.y == 0.0f) | (v.z == 0.0f) | (v.w == 0.0f);
+          b |= ((v.x < 0.0f ? 1u : 0u) | (v.y < 0.0f ? 2u : 0u) | (v.z < 0.0f ? 4u : 0u) |
+                (v.w < 0.0f ? 8u : 0u)) << j;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const float v = Store<S>::ld(q + j);
+          z |= (v == 0.0f);
+          b |= (v < 0.0f ? 1u : 0u) << j;
         }
       }
+      if (r < 8) words[r] = b;
+      else beta[w0 + i] = b;             // beyond the register window: park directly
+    }
+    if (__any_sync(FULL, z)) return false;
+    for (uint32_t i = lane, r = 0; i < nw && r < 8; i += 32, ++r) beta[w0 + i] = words[r];
+    if (UH) {
+      __syncwarp();
+      for (uint32_t i = lane; i < nw; i += 32) uh[w0 + i] = encode_word(beta[w0 + i], 5);
       xword_encode(uh, w0, nw);
     } else {
-      bool d = (uint32_t)lane < n ? (Store<S>::ld(Lk + lane) < 0.0f) : false;
-      uint32_t b = __ballot_sync(FULL, d) & low_mask(n);
-      if (lane == 0) {
-        insert(beta, o, n, b);
-        insert(uh, o, n, encode_word(b, k));
-      }
       __syncwarp();
     }
     return true;
@@ -344,7 +372,7 @@ __host__ __device__ inline uint32_t bit_words(int t) {
   return (4 * W + 2 * CW + 3u) & ~3u;
 }
 
-template <typename S, int FK, bool SC>
+template <typename S, int FK, bool SC, bool UH>
 __global__ void __launch_bounds__(32) k_subtree(StParams p, bool in_is_llr) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int t = p.t;
@@ -378,22 +406,61 @@ __global__ void __launch_bounds__(32) k_subtree(StParams p, bool in_is_llr) {
   if (SC && p.cls)
     for (uint32_t i = lane; i < 2 * CW; i += 32) ctab[i] = p.cls[i];
   S *Lt = w.lvl(t);
+  // Level-t LLRs into shared memory with 16-byte loads, eight in flight per
+  // lane (one warp would otherwise wait a memory latency per element).
   if (in_is_llr) {
-    const float *src = reinterpret_cast<const float *>(p.in) + fr * p.in_stride;
-    for (uint32_t i = lane; i < T; i += 32) Store<S>::st(Lt + i, src[i] * w.sc);
+    const float *src = reinterpret_cast<const float *>(p.in) + fr * p.in_stride + p.o;
+    if (T >= 4) {
+      const float4 *s4 = reinterpret_cast<const float4 *>(src);
+      for (uint32_t b = 0; b < T / 4; b += 32 * 8) {
+        float4 q[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const uint32_t i = b + 32 * r + lane;
+          if (i < T / 4) q[r] = s4[i];
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const uint32_t i = b + 32 * r + lane;
+          if (i < T / 4) {
+            Store<S>::st(Lt + 4 * i, q[r].x * w.sc);
+            Store<S>::st(Lt + 4 * i + 1, q[r].y * w.sc);
+            Store<S>::st(Lt + 4 * i + 2, q[r].z * w.sc);
+            Store<S>::st(Lt + 4 * i + 3, q[r].w * w.sc);
+          }
+        }
+      }
+    } else {
+      for (uint32_t i = lane; i < T; i += 32) Store<S>::st(Lt + i, src[i] * w.sc);
+    }
   } else {
     const S *src = reinterpret_cast<const S *>(p.in) + fr * p.in_stride;
-    for (uint32_t i = lane; i < T; i += 32) Lt[i] = src[i];
+    const uint32_t n16 = (uint32_t)(T * sizeof(S) / 16);   // T * sizeof(S) >= 32 here
+    const uint4 *s16 = reinterpret_cast<const uint4 *>(src);
+    uint4 *d16 = reinterpret_cast<uint4 *>(Lt);
+    for (uint32_t b = 0; b < n16; b += 32 * 8) {
+      uint4 q[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const uint32_t i = b + 32 * r + lane;
+        if (i < n16) q[r] = s16[i];
+      }
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const uint32_t i = b + 32 * r + lane;
+        if (i < n16) d16[i] = q[r];
+      }
+    }
   }
   __syncwarp();
 
   if (SC && t < 5) {
     // whole code shorter than a word: one register block with class checks
     switch (t) {
-      case 1: w.template leafblock<1, FK, true>(0); break;
-      case 2: w.template leafblock<2, FK, true>(0); break;
-      case 3: w.template leafblock<3, FK, true>(0); break;
-      default: w.template leafblock<4, FK, true>(0); break;
+      case 1: w.template leafblock<1, FK, true, UH>(0); break;
+      case 2: w.template leafblock<2, FK, true, UH>(0); break;
+      case 3: w.template leafblock<3, FK, true, UH>(0); break;
+      default: w.template leafblock<4, FK, true, UH>(0); break;
     }
   } else {
     int k = t;
@@ -403,12 +470,12 @@ __global__ void __launch_bounds__(32) k_subtree(StParams p, bool in_is_llr) {
         if (SC) {
           const int cls = w.cls_tab(k, o);
           if (cls == NODE_RATE0) {
-            w.rate0(k, o);
+            w.template rate0<UH>(k, o);
             break;
           }
-          if (cls == NODE_RATE1 && w.rate1(k, o)) break;
+          if (cls == NODE_RATE1 && w.template rate1<UH>(k, o)) break;
           if (k == 5) {
-            w.template leafblock<5, FK, false>(o);
+            w.template leafblock<5, FK, false, UH>(o);
             break;
           }
           if (k - 1 < 5 || w.cls_tab(k - 1, o) != NODE_RATE0) w.template f<FK>(k);
@@ -443,13 +510,13 @@ __global__ void __launch_bounds__(32) k_subtree(StParams p, bool in_is_llr) {
   if (p.r > 0) cascade_device(p.xhat + fr * p.w_stride, t, p.o, p.r);
 }
 
-template <typename S, int FK, bool SC>
+template <typename S, int FK, bool SC, bool UH>
 cudaError_t launch_t(const SubtreeArgs &a, cudaStream_t s) {
   const uint32_t T = 1u << a.t;
   const uint32_t W = T >= 32 ? T / 32 : 1;
   (void)W;
   size_t smem = bit_words(a.t) * sizeof(uint32_t) + 2 * (size_t)T * sizeof(S);
-  auto kern = k_subtree<S, FK, SC>;
+  auto kern = k_subtree<S, FK, SC, UH>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
@@ -463,9 +530,13 @@ cudaError_t launch_t(const SubtreeArgs &a, cudaStream_t s) {
 
 template <typename S>
 cudaError_t launch_s(const SubtreeArgs &a, cudaStream_t s) {
-  if (a.fkind == 0)
-    return a.shortcuts ? launch_t<S, 0, true>(a, s) : launch_t<S, 0, false>(a, s);
-  return a.shortcuts ? launch_t<S, 1, true>(a, s) : launch_t<S, 1, false>(a, s);
+  const bool uh = a.uhat != nullptr;
+  if (a.fkind == 0) {
+    if (!a.shortcuts) return launch_t<S, 0, false, true>(a, s);
+    return uh ? launch_t<S, 0, true, true>(a, s) : launch_t<S, 0, true, false>(a, s);
+  }
+  if (!a.shortcuts) return launch_t<S, 1, false, true>(a, s);
+  return uh ? launch_t<S, 1, true, true>(a, s) : launch_t<S, 1, true, false>(a, s);
 }
 
 }  // namespace

@@ -158,3 +158,44 @@ def frames(w: Workload, first: int, count: int):
         xs.append(x)
         ys.append(y)
     return np.stack(xs), np.stack(ys)
+
+
+# ------------------------------------------------------------------ device-side draws
+# For streams too large to draw on the host (the served mixed workload), the
+# same distributions are drawn on the GPU with torch's Philox generator,
+# seeded per request.  Only random draws and bit packing happen here.
+def _gen(seed: int, idx: int, device):
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(_mix(np.array([(seed * GAMMA + idx) & 0xFFFFFFFFFFFFFFFF],
+                                    dtype=np.uint64))[0]) & 0x7FFFFFFFFFFFFFFF)
+    return g
+
+
+def pack_bits_torch(bits):
+    """bool/0-1 tensor [..., N] -> int32 words [..., N/32] (little-endian)."""
+    import torch
+    b = bits.to(torch.int64).reshape(*bits.shape[:-1], -1, 32)
+    w = (b << torch.arange(32, device=bits.device, dtype=torch.int64)).sum(-1)
+    return (w & 0xFFFFFFFF).to(torch.int64).where(w < 2 ** 31, w - 2 ** 32).to(torch.int32)
+
+
+def unpack_bits_torch(words, N: int):
+    import torch
+    w = words.to(torch.int64) & 0xFFFFFFFF
+    b = (w.unsqueeze(-1) >> torch.arange(32, device=words.device, dtype=torch.int64)) & 1
+    return b.reshape(*words.shape[:-1], -1)[..., :N]
+
+
+def device_frame(channel: str, param: float, N: int, seed: int, idx: int, device):
+    """(x words int32 [N/32], y) on the device: y packed int32 words (BSC) or
+    float64 [N] (BI-AWGN, y = (1 - 2x) + sqrt(sigma^2) z)."""
+    import torch
+    g = _gen(seed, idx, device)
+    xb = torch.randint(0, 2, (N,), generator=g, device=device, dtype=torch.int32)
+    x = pack_bits_torch(xb)
+    if channel == "bsc":
+        e = torch.rand(N, generator=g, device=device, dtype=torch.float64) < param
+        return x, pack_bits_torch(xb.bool() ^ e)
+    z = torch.randn(N, generator=g, device=device, dtype=torch.float64)
+    return x, (1.0 - 2.0 * xb.to(torch.float64)) + math.sqrt(param) * z
