@@ -118,7 +118,22 @@ __device__ __forceinline__ void cascade_device(uint32_t *x, int ku, uint64_t ou,
     uint64_t base = (ou >> (L + 1)) << (L + 1);
     uint64_t hw = (uint64_t(1) << L) >> 5;
     uint32_t *left = x + (base >> 5);
-    for (uint64_t i = threadIdx.x; i < hw; i += blockDim.x) left[i] ^= left[hw + i];
+    for (uint64_t b = threadIdx.x; b < hw; b += (uint64_t)blockDim.x * 8) {
+      uint32_t a[8], c[8];                       // eight loads in flight per thread
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const uint64_t i = b + (uint64_t)q * blockDim.x;
+        if (i < hw) {
+          a[q] = left[i];
+          c[q] = left[hw + i];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const uint64_t i = b + (uint64_t)q * blockDim.x;
+        if (i < hw) left[i] = a[q] ^ c[q];
+      }
+    }
     __syncthreads();
   }
 }

@@ -1,0 +1,6 @@
+// FP16-storage instantiation of the subtree decoder (see subtree_impl.cuh).
+#include "subtree_impl.cuh"
+
+namespace polar {
+cudaError_t launch_subtree_f16(const SubtreeArgs &a, cudaStream_t s) { return launch_s<__half>(a, s); }
+}  // namespace polar

@@ -1,0 +1,710 @@
+// In-CTA subtree decoder: one warp runs the SC recursion (Sec. 4) over a
+// node of 2^t leaves whose LLRs sit in shared memory, one CTA per frame.
+//
+// Shared memory: level k of the recursion (2^k LLRs) lives at L[2^k, 2^(k+1)),
+// level t (the input) at L[2^t, 2^(t+1)); bit vectors beta (partial sums, in
+// place), u_hat, the frozen mask and the frozen values take 2^t bits each.
+//
+// Node shortcuts (when enabled) return the exact SC result:
+//   rate 0 (all frozen): beta = fv F^{(x)k} -- SC decides every leaf from fv
+//                        and beta is the transform of the decisions;
+//   rate 1 (all info):   beta = hard(L) when no input LLR is +-0 -- by
+//                        induction f(a, b) has the sign product and g then
+//                        reproduces sgn(b), so each leaf's decision is the
+//                        hard decision of its input; a zero input falls back
+//                        to the full recursion.
+//
+// With shortcuts on, node classes of the levels 5..t come from a table the
+// host precomputes per subtree, and every mixed node of 32 leaves is decoded
+// in registers by a fully unrolled recursion (all lanes run it redundantly;
+// no shuffles, no shared-memory round trips below 32 leaves).  The plain
+// variant (shortcuts off) runs every level lane-parallel through shared
+// memory down to single leaves.
+#pragma once
+
+#include "device_common.cuh"
+#include "polar_internal.h"
+
+namespace polar {
+
+namespace {
+
+constexpr uint32_t FULL = 0xFFFFFFFFu;
+
+struct StParams {
+  const void *in;
+  size_t in_stride;
+  const uint32_t *cls;   // class table of this subtree (levels 5..t), or null
+  const float *scale;    // per-frame int8 scale, or null
+  const uint32_t *mask;
+  const uint32_t *fv;
+  uint32_t *xhat;
+  uint32_t *uhat;
+  size_t w_stride;
+  uint64_t o;
+  int t;
+  int r;
+};
+
+// g with the partial sum taken from bit j of a word: b + a or b - a (the
+// latter as b + (-a), which IEEE addition makes identical).
+__device__ __forceinline__ float g_bit(float a, float b, uint32_t word, int j) {
+  return b + __uint_as_float(__float_as_uint(a) ^ ((word << (31 - j)) & 0x80000000u));
+}
+
+// Rate-1 test of a node held in registers: true (and the sign word in *b)
+// when no input is +-0; min and OR trees keep the dependency depth at K.
+template <int K>
+__device__ __forceinline__ bool signs_if_nonzero(const float (&a)[1 << K], uint32_t *b) {
+  constexpr int N = 1 << K;
+  float m[N];
+  uint32_t v[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    m[j] = fabsf(a[j]);
+    v[j] = (__float_as_uint(a[j]) >> 31) << j;
+  }
+#pragma unroll
+  for (int w = N / 2; w >= 1; w /= 2) {
+#pragma unroll
+    for (int j = 0; j < w; ++j) {
+      m[j] = fminf(m[j], m[j + w]);
+      v[j] |= v[j + w];
+    }
+  }
+  *b = v[0];
+  return m[0] > 0.0f;
+}
+
+// SC over a node of 2^K leaves held in registers: returns beta (2^K bits)
+// and u_hat in `u`.  frz / fv are the node's mask and frozen values in the
+// low 2^K bits.  CHECK: test the node itself for rate 0 / rate 1 first.
+// Nodes of up to 4 leaves take the generic path without class branches.
+template <int K, int FK, bool CHECK, typename S>
+struct Dec {
+  static constexpr int N = 1 << K, H = N / 2;
+  static __device__ __forceinline__ uint32_t run(const float (&a)[N], uint32_t frz, uint32_t fv,
+                                                 uint32_t &u, float sc) {
+    constexpr uint32_t M = (N == 32) ? 0xFFFFFFFFu : ((1u << N) - 1u);
+    constexpr uint32_t MH = (1u << H) - 1u;
+    if (CHECK && K >= 5) {
+      if (frz == M) {
+        u = fv;
+        return encode_word(fv, K);
+      }
+      if (frz == 0u) {
+        uint32_t b;
+        if (signs_if_nonzero<K>(a, &b)) {   // no zero input: signs are the decisions
+          u = encode_word(b, K);
+          return b;
+        }
+      }
+    }
+    float l[H];
+    uint32_t uL, bL;
+    const uint32_t fzL = frz & MH, fvL = fv & MH;
+    if (K >= 3 && fzL == MH) {     // rate-0 left child: its f is never needed
+      uL = fvL;
+      bL = encode_word(fvL, K - 1);
+    } else {
+#pragma unroll
+      for (int j = 0; j < H; ++j) l[j] = rnd<S>(f_st<S, FK>(a[j], a[j + H], sc));
+      bL = Dec<K - 1, FK, true, S>::run(l, fzL, fvL, uL, sc);
+    }
+#pragma unroll
+    for (int j = 0; j < H; ++j) l[j] = rnd<S>(g_bit(a[j], a[j + H], bL, j));
+    uint32_t uR;
+    const uint32_t bR = Dec<K - 1, FK, true, S>::run(l, frz >> H, fv >> H, uR, sc);
+    u = uL | (uR << H);
+    return (bL ^ bR) | (bR << H);
+  }
+};
+
+template <int FK, bool CHECK, typename S>
+struct Dec<0, FK, CHECK, S> {
+  static __device__ __forceinline__ uint32_t run(const float (&a)[1], uint32_t frz, uint32_t fv,
+                                                 uint32_t &u, float) {
+    u = (frz & 1u) ? (fv & 1u) : (a[0] < 0.0f ? 1u : 0u);
+    return u;
+  }
+};
+
+// ---------------------------------------------------------------- register tiles
+// A node of 2^K leaves, 5 <= K <= 9, decoded in registers: element j of the
+// node sits in lane j % 32, register j / 32, so every f and g of the levels
+// 6..K pairs values of the same lane.  Masks, frozen values and partial sums
+// are uniform words (identical in every lane).  A mixed node of 32 leaves is
+// gathered through shared memory into every lane and decoded by Dec<5>.
+
+// Mixed or shortcut 32-leaf node; v = this lane's LLR.  Returns beta in the low
+// word and u_hat in the high word.
+template <int FK, typename S, bool UH>
+__device__ __noinline__ uint64_t tile32(float v, uint32_t m, uint32_t fv, float sc, float *gbuf,
+                                        int lane) {
+  if (m == FULL) return (uint64_t)encode_word(fv, 5) | ((uint64_t)fv << 32);
+  if (m == 0u && !__any_sync(FULL, v == 0.0f)) {
+    const uint32_t b = __ballot_sync(FULL, v < 0.0f);
+    return (uint64_t)b | ((uint64_t)(UH ? encode_word(b, 5) : 0u) << 32);
+  }
+  gbuf[lane] = v;
+  __syncwarp();
+  float a[32];
+#pragma unroll
+  for (int j = 0; j < 32; j += 4) {
+    const float4 q = *reinterpret_cast<const float4 *>(gbuf + j);
+    a[j] = q.x;
+    a[j + 1] = q.y;
+    a[j + 2] = q.z;
+    a[j + 3] = q.w;
+  }
+  __syncwarp();
+  uint32_t u;
+  const uint32_t b = Dec<5, FK, false, S>::run(a, m, fv, u, sc);
+  return (uint64_t)b | ((uint64_t)u << 32);
+}
+
+template <int K, int FK, typename S, bool UH>
+struct Tile {
+  static constexpr int R = 1 << (K - 5), H = R / 2;
+  static __device__ __forceinline__ void run(const float (&v)[R], const uint32_t *m,
+                                             const uint32_t *fv, uint32_t (&bo)[R],
+                                             uint32_t (&uo)[R], float sc, float *gbuf, int lane) {
+    bool all1 = true, all0 = true;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      all1 &= (m[r] == FULL);
+      all0 &= (m[r] == 0u);
+    }
+    if (all1) {                                   // rate 0
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        bo[r] = encode_word(fv[r], 5);
+        uo[r] = fv[r];
+      }
+#pragma unroll
+      for (int hw = 1; hw < R; hw *= 2)
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          if (!(r & hw)) bo[r] ^= bo[r + hw];
+      return;
+    }
+    if (all0) {                                   // rate 1, unless some input is +-0
+      bool z = false;
+#pragma unroll
+      for (int r = 0; r < R; ++r) z |= (v[r] == 0.0f);
+      if (!__any_sync(FULL, z)) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) bo[r] = __ballot_sync(FULL, v[r] < 0.0f);
+        if (UH) {
+#pragma unroll
+          for (int r = 0; r < R; ++r) uo[r] = encode_word(bo[r], 5);
+#pragma unroll
+          for (int hw = 1; hw < R; hw *= 2)
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+              if (!(r & hw)) uo[r] ^= uo[r + hw];
+        }
+        return;
+      }
+    }
+    float c[H];
+    uint32_t bL[H], uL[H], bR[H], uR[H];
+    bool left0 = true;
+#pragma unroll
+    for (int r = 0; r < H; ++r) left0 &= (m[r] == FULL);
+    if (left0) {                                  // rate-0 left child: no f needed
+#pragma unroll
+      for (int r = 0; r < H; ++r) {
+        bL[r] = encode_word(fv[r], 5);
+        uL[r] = fv[r];
+      }
+#pragma unroll
+      for (int hw = 1; hw < H; hw *= 2)
+#pragma unroll
+        for (int r = 0; r < H; ++r)
+          if (!(r & hw)) bL[r] ^= bL[r + hw];
+    } else {
+#pragma unroll
+      for (int r = 0; r < H; ++r) c[r] = rnd<S>(f_st<S, FK>(v[r], v[r + H], sc));
+      Tile<K - 1, FK, S, UH>::run(c, m, fv, bL, uL, sc, gbuf, lane);
+    }
+    const int sh = 31 - lane;
+#pragma unroll
+    for (int r = 0; r < H; ++r)
+      c[r] = rnd<S>(v[r + H] + __uint_as_float(__float_as_uint(v[r]) ^
+                                              ((bL[r] << sh) & 0x80000000u)));
+    Tile<K - 1, FK, S, UH>::run(c, m + H, fv + H, bR, uR, sc, gbuf, lane);
+#pragma unroll
+    for (int r = 0; r < H; ++r) {
+      bo[r] = bL[r] ^ bR[r];
+      bo[r + H] = bR[r];
+      uo[r] = uL[r];
+      uo[r + H] = uR[r];
+    }
+  }
+};
+
+template <int FK, typename S, bool UH>
+struct Tile<5, FK, S, UH> {
+  static __device__ __forceinline__ void run(const float (&v)[1], const uint32_t *m,
+                                             const uint32_t *fv, uint32_t (&bo)[1],
+                                             uint32_t (&uo)[1], float sc, float *gbuf, int lane) {
+    const uint64_t r = tile32<FK, S, UH>(v[0], m[0], fv[0], sc, gbuf, lane);
+    bo[0] = (uint32_t)r;
+    uo[0] = (uint32_t)(r >> 32);
+  }
+};
+
+template <typename S>
+struct Warp {
+  S *L;
+  uint32_t *beta, *uh, *msk, *fvw;
+  const uint32_t *cr0, *cr1;   // class table: bit 2^(t-k) + (o >> k) for level k >= 5
+  int lane, t;
+  float sc;                    // int8 per-frame scale (1 otherwise)
+  float *gbuf;                 // 32 floats: gather buffer of the register tiles
+
+  // Node of 2^K leaves (5 <= K <= 9) at leaf o, decoded by a register tile.
+  template <int K, int FK, bool UH>
+  __device__ void tile(uint32_t o) const {
+    constexpr int R = 1 << (K - 5);
+    const S *src = lvl(K);
+    float v[R];
+    uint32_t m[R], fv[R], bo[R], uo[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      v[r] = Store<S>::ld(src + 32 * r + lane);
+      m[r] = msk[(o >> 5) + r];
+      fv[r] = fvw[(o >> 5) + r];
+    }
+    Tile<K, FK, S, UH>::run(v, m, fv, bo, uo, sc, gbuf, lane);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (lane == r) {
+        beta[(o >> 5) + r] = bo[r];
+        if (UH) uh[(o >> 5) + r] = uo[r];
+      }
+    }
+    __syncwarp();
+  }
+
+  template <int FK, bool UH>
+  __device__ void tile_k(int k, uint32_t o) const {
+    switch (k) {
+      case 5: tile<5, FK, UH>(o); break;
+      case 6: tile<6, FK, UH>(o); break;
+      case 7: tile<7, FK, UH>(o); break;
+      case 8: tile<8, FK, UH>(o); break;
+      default: tile<9, FK, UH>(o); break;
+    }
+  }
+
+  __device__ __forceinline__ S *lvl(int k) const { return L + (1u << k); }
+
+  // Class of a node of level k >= 5 from the table.
+  __device__ __forceinline__ int cls_tab(int k, uint32_t o) const {
+    uint32_t i = (1u << (t - k)) + (o >> k);
+    uint32_t b0 = (cr0[i >> 5] >> (i & 31)) & 1u, b1 = (cr1[i >> 5] >> (i & 31)) & 1u;
+    return b0 ? NODE_RATE0 : (b1 ? NODE_RATE1 : NODE_MIXED);
+  }
+
+  // Mixed node of 2^K leaves (K <= 5) at leaf o, decoded in registers.
+  template <int K, int FK, bool CHECK, bool UH>
+  __device__ void leafblock(uint32_t o) const {
+    constexpr int N = 1 << K;
+    const S *src = lvl(K);
+    float a[N];
+    if constexpr (sizeof(S) == 4 && N >= 4) {     // level K starts 16-byte aligned
+#pragma unroll
+      for (int j = 0; j < N; j += 4) {
+        float4 q = *reinterpret_cast<const float4 *>(src + j);
+        a[j] = q.x;
+        a[j + 1] = q.y;
+        a[j + 2] = q.z;
+        a[j + 3] = q.w;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < N; ++j) a[j] = Store<S>::ld(src + j);
+    }
+    const uint32_t m = N == 32 ? 0xFFFFFFFFu : ((1u << N) - 1u);
+    const uint32_t sh = o & 31;
+    uint32_t u;
+    uint32_t b =
+        Dec<K, FK, CHECK, S>::run(a, (msk[o >> 5] >> sh) & m, (fvw[o >> 5] >> sh) & m, u, sc);
+    if (lane == 0) {
+      insert(beta, o, N, b);
+      if (UH) insert(uh, o, N, u);
+    }
+    __syncwarp();
+  }
+
+  __device__ int node_class(int k, uint32_t o) const {
+    if (k < 5) {
+      uint32_t m = low_mask(1 << k);
+      uint32_t b = (msk[o >> 5] >> (o & 31)) & m;
+      return b == m ? NODE_RATE0 : (b == 0 ? NODE_RATE1 : NODE_MIXED);
+    }
+    uint32_t nw = 1u << (k - 5), w0 = o >> 5;
+    bool all1 = true, all0 = true;
+    for (uint32_t i = lane; i < nw; i += 32) {
+      uint32_t v = msk[w0 + i];
+      all1 &= (v == FULL);
+      all0 &= (v == 0u);
+    }
+    all1 = __all_sync(FULL, all1);
+    all0 = __all_sync(FULL, all0);
+    return all1 ? NODE_RATE0 : (all0 ? NODE_RATE1 : NODE_MIXED);
+  }
+
+  // Cross-word transform levels of the words [w0, w0 + nw) of `v`.
+  __device__ void xword_encode(uint32_t *v, uint32_t w0, uint32_t nw) const {
+    for (uint32_t hw = 1; hw < nw; hw <<= 1) {
+      __syncwarp();
+      for (uint32_t j = lane; j < nw / 2; j += 32) {
+        uint32_t a = (j / hw) * 2 * hw + (j % hw);
+        v[w0 + a] ^= v[w0 + a + hw];
+      }
+    }
+    __syncwarp();
+  }
+
+  __device__ void insert(uint32_t *v, uint32_t o, int nbits, uint32_t bits) const {
+    uint32_t m = low_mask(nbits) << (o & 31);
+    v[o >> 5] = (v[o >> 5] & ~m) | ((bits << (o & 31)) & m);
+  }
+
+  template <bool UH = true>
+  __device__ void rate0(int k, uint32_t o) const {
+    if (k >= 5) {
+      uint32_t w0 = o >> 5, nw = 1u << (k - 5);
+      for (uint32_t i = lane; i < nw; i += 32) {
+        uint32_t v = fvw[w0 + i];
+        if (UH) uh[w0 + i] = v;
+        beta[w0 + i] = encode_word(v, 5);
+      }
+      xword_encode(beta, w0, nw);
+    } else {
+      if (lane == 0) {
+        uint32_t v = (fvw[o >> 5] >> (o & 31)) & low_mask(1 << k);
+        insert(uh, o, 1 << k, v);
+        insert(beta, o, 1 << k, encode_word(v, k));
+      }
+      __syncwarp();
+    }
+  }
+
+  // Rate-1 shortcut (k >= 5); false (nothing written) when some input is +-0.
+  // Each lane builds whole words of hard decisions (32 LLRs per word), so a
+  // node costs one pass over its LLRs and one vote.
+  template <bool UH>
+  __device__ bool rate1(int k, uint32_t o) const {
+    const S *Lk = lvl(k);
+    const uint32_t w0 = o >> 5, nw = 1u << (k - 5);
+    if (nw == 1) {
+      const float v = Store<S>::ld(Lk + lane);
+      if (__any_sync(FULL, v == 0.0f)) return false;
+      const uint32_t b = __ballot_sync(FULL, v < 0.0f);
+      if (lane == 0) {
+        beta[w0] = b;
+        if (UH) uh[w0] = encode_word(b, 5);
+      }
+      __syncwarp();
+      return true;
+    }
+    bool z = false;
+    uint32_t words[8];                   // nw <= 2^(t-5) <= 512: 16 words per lane at most
+#pragma unroll
+    for (int r = 0; r < 8; ++r) words[r] = 0u;
+    for (uint32_t i = lane, r = 0; i < nw; i += 32, ++r) {
+      uint32_t b = 0u;
+      const S *q = Lk + 32 * i;
+      if constexpr (sizeof(S) == 4) {   // level k >= 6 starts 16-byte aligned
+#pragma unroll
+        for (int j = 0; j < 32; j += 4) {
+          const float4 v = *reinterpret_cast<const float4 *>(q + j);
+          z |= (v.x == 0.0f) | (v.y == 0.0f) | (v.z == 0.0f) | (v.w == 0.0f);
+          b |= ((v.x < 0.0f ? 1u : 0u) | (v.y < 0.0f ? 2u : 0u) | (v.z < 0.0f ? 4u : 0u) |
+                (v.w < 0.0f ? 8u : 0u)) << j;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const float v = Store<S>::ld(q + j);
+          z |= (v == 0.0f);
+          b |= (v < 0.0f ? 1u : 0u) << j;
+        }
+      }
+      if (r < 8) words[r] = b;
+      else beta[w0 + i] = b;             // beyond the register window: park directly
+    }
+    if (__any_sync(FULL, z)) return false;
+    for (uint32_t i = lane, r = 0; i < nw && r < 8; i += 32, ++r) beta[w0 + i] = words[r];
+    if (UH) {
+      __syncwarp();
+      for (uint32_t i = lane; i < nw; i += 32) uh[w0 + i] = encode_word(beta[w0 + i], 5);
+      xword_encode(uh, w0, nw);
+    } else {
+      __syncwarp();
+    }
+    return true;
+  }
+
+  __device__ void leaf(uint32_t o) const {
+    if (lane == 0) {
+      uint32_t w = o >> 5, s = o & 31;
+      uint32_t u = ((msk[w] >> s) & 1u) ? ((fvw[w] >> s) & 1u)
+                                        : (uint32_t)(Store<S>::ld(lvl(0)) < 0.0f);
+      insert(beta, o, 1, u);
+      insert(uh, o, 1, u);
+    }
+    __syncwarp();
+  }
+
+  template <int FK>
+  __device__ void f(int k) const {
+    const S *__restrict__ a = lvl(k);
+    S *__restrict__ c = lvl(k - 1);
+    const uint32_t h = 1u << (k - 1);
+    if (h >= 128) {
+      for (uint32_t i = lane; i < h; i += 128) {
+        float x[4], y[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          x[q] = Store<S>::ld(a + i + 32 * q);
+          y[q] = Store<S>::ld(a + h + i + 32 * q);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) Store<S>::st(c + i + 32 * q, f_st<S, FK>(x[q], y[q], sc));
+      }
+    } else {
+      for (uint32_t i = lane; i < h; i += 32)
+        Store<S>::st(c + i, f_st<S, FK>(Store<S>::ld(a + i), Store<S>::ld(a + h + i), sc));
+    }
+    __syncwarp();
+  }
+
+  // Right child of the node of level k whose left child starts at leaf o.
+  __device__ void g(int k, uint32_t o) const {
+    const S *__restrict__ a = lvl(k);
+    S *__restrict__ c = lvl(k - 1);
+    const uint32_t h = 1u << (k - 1);
+    if (h >= 128) {
+      for (uint32_t i = lane; i < h; i += 128) {
+        float x[4], y[4];
+        uint32_t wd[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          x[q] = Store<S>::ld(a + i + 32 * q);
+          y[q] = Store<S>::ld(a + h + i + 32 * q);
+          wd[q] = beta[(o + i + 32 * q) >> 5];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          Store<S>::st(c + i + 32 * q, g_bit(x[q], y[q], wd[q], (o + i) & 31));
+      }
+    } else {
+      for (uint32_t i = lane; i < h; i += 32) {
+        uint32_t p = o + i;
+        Store<S>::st(c + i, g_bit(Store<S>::ld(a + i), Store<S>::ld(a + h + i), beta[p >> 5],
+                                  p & 31));
+      }
+    }
+    __syncwarp();
+  }
+
+  // Parent of level K at leaf base: left half ^= right half.
+  __device__ void combine(int K, uint32_t base) const {
+    const uint32_t h = 1u << (K - 1);
+    if (h >= 32) {
+      uint32_t w0 = base >> 5, hw = h >> 5;
+      for (uint32_t i = lane; i < hw; i += 32) beta[w0 + i] ^= beta[w0 + hw + i];
+    } else if (lane == 0) {
+      uint32_t w = beta[base >> 5], s = base & 31;
+      uint32_t r = (w >> (s + h)) & low_mask(h);
+      beta[base >> 5] = w ^ (r << s);
+    }
+    __syncwarp();
+  }
+};
+
+// Words of shared memory before the LLR levels: beta, u_hat, mask, frozen
+// values (W each), the two class-table halves (CW each), rounded up to 16 B,
+// then the 32-float gather buffer of the register tiles.
+__host__ __device__ inline uint32_t bit_words(int t) {
+  const uint32_t W = t >= 5 ? (1u << (t - 5)) : 1u;
+  const uint32_t CW = t >= 9 ? (1u << (t - 9)) : 1u;
+  return ((4 * W + 2 * CW + 3u) & ~3u) + 32u;
+}
+
+template <typename S, int FK, bool SC, bool UH>
+__global__ void __launch_bounds__(32) k_subtree(StParams p, bool in_is_llr) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int t = p.t;
+  const uint32_t T = 1u << t;
+  const uint32_t W = T >= 32 ? T / 32 : 1;
+  const uint32_t CW = t >= 9 ? (1u << (t - 9)) : 1u;
+  const int lane = threadIdx.x;
+  const size_t fr = blockIdx.x;
+
+  Warp<S> w;
+  w.lane = lane;
+  w.t = t;
+  w.sc = p.scale ? p.scale[fr] : 1.0f;
+  w.beta = reinterpret_cast<uint32_t *>(smraw);
+  w.uh = w.beta + W;
+  w.msk = w.beta + 2 * W;
+  w.fvw = w.beta + 3 * W;
+  uint32_t *ctab = w.beta + 4 * W;
+  w.cr0 = ctab;
+  w.cr1 = ctab + CW;
+  w.L = reinterpret_cast<S *>(w.beta + bit_words(t));
+  w.gbuf = reinterpret_cast<float *>(w.beta + bit_words(t) - 32);
+
+  const uint64_t ow = p.o >> 5;
+  const uint32_t *fvf = p.fv + fr * p.w_stride + ow;
+  for (uint32_t i = lane; i < W; i += 32) {
+    w.msk[i] = p.mask[ow + i];
+    w.fvw[i] = fvf[i];
+    w.beta[i] = 0u;
+    w.uh[i] = 0u;
+  }
+  if (SC && p.cls)
+    for (uint32_t i = lane; i < 2 * CW; i += 32) ctab[i] = p.cls[i];
+  S *Lt = w.lvl(t);
+  // Level-t LLRs into shared memory with 16-byte loads, eight in flight per
+  // lane (one warp would otherwise wait a memory latency per element).
+  if (in_is_llr) {
+    const float *src = reinterpret_cast<const float *>(p.in) + fr * p.in_stride + p.o;
+    if (T >= 4) {
+      const float4 *s4 = reinterpret_cast<const float4 *>(src);
+      for (uint32_t b = 0; b < T / 4; b += 32 * 8) {
+        float4 q[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const uint32_t i = b + 32 * r + lane;
+          if (i < T / 4) q[r] = s4[i];
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const uint32_t i = b + 32 * r + lane;
+          if (i < T / 4) {
+            Store<S>::st(Lt + 4 * i, q[r].x * w.sc);
+            Store<S>::st(Lt + 4 * i + 1, q[r].y * w.sc);
+            Store<S>::st(Lt + 4 * i + 2, q[r].z * w.sc);
+            Store<S>::st(Lt + 4 * i + 3, q[r].w * w.sc);
+          }
+        }
+      }
+    } else {
+      for (uint32_t i = lane; i < T; i += 32) Store<S>::st(Lt + i, src[i] * w.sc);
+    }
+  } else {
+    const S *src = reinterpret_cast<const S *>(p.in) + fr * p.in_stride;
+    const uint32_t n16 = (uint32_t)(T * sizeof(S) / 16);   // T * sizeof(S) >= 32 here
+    const uint4 *s16 = reinterpret_cast<const uint4 *>(src);
+    uint4 *d16 = reinterpret_cast<uint4 *>(Lt);
+    for (uint32_t b = 0; b < n16; b += 32 * 8) {
+      uint4 q[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const uint32_t i = b + 32 * r + lane;
+        if (i < n16) q[r] = s16[i];
+      }
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const uint32_t i = b + 32 * r + lane;
+        if (i < n16) d16[i] = q[r];
+      }
+    }
+  }
+  __syncwarp();
+
+  if (SC && t < 5) {
+    // whole code shorter than a word: one register block with class checks
+    switch (t) {
+      case 1: w.template leafblock<1, FK, true, UH>(0); break;
+      case 2: w.template leafblock<2, FK, true, UH>(0); break;
+      case 3: w.template leafblock<3, FK, true, UH>(0); break;
+      default: w.template leafblock<4, FK, true, UH>(0); break;
+    }
+  } else {
+    int k = t;
+    uint32_t o = 0;
+    for (;;) {
+      for (;;) {                                 // descend
+        if (SC) {
+          if (k <= 9) {                          // register tile (k = min(t, 9))
+            w.template tile_k<FK, UH>(k, o);
+            break;
+          }
+          const int cls = w.cls_tab(k, o);
+          if (cls == NODE_RATE0) {
+            w.template rate0<UH>(k, o);
+            break;
+          }
+          if (cls == NODE_RATE1 && w.template rate1<UH>(k, o)) break;
+          if (w.cls_tab(k - 1, o) != NODE_RATE0) w.template f<FK>(k);
+        } else {
+          if (k == 0) {
+            w.leaf(o);
+            break;
+          }
+          w.template f<FK>(k);
+        }
+        --k;
+      }
+      while (k < t && ((o >> k) & 1u)) {         // ascend through right children
+        w.combine(k + 1, o - (1u << k));
+        o -= 1u << k;
+        ++k;
+      }
+      if (k == t) break;
+      w.g(k + 1, o);                             // right sibling's LLRs
+      o += 1u << k;
+    }
+  }
+
+  uint32_t *xf = p.xhat + fr * p.w_stride + ow;
+  uint32_t *uf = p.uhat ? p.uhat + fr * p.w_stride + ow : nullptr;
+  const uint32_t keep = T >= 32 ? FULL : low_mask(T);
+  for (uint32_t i = lane; i < W; i += 32) {
+    xf[i] = w.beta[i] & keep;
+    if (uf) uf[i] = w.uh[i] & keep;
+  }
+  __syncthreads();
+  if (p.r > 0) cascade_device(p.xhat + fr * p.w_stride, t, p.o, p.r);
+}
+
+template <typename S, int FK, bool SC, bool UH>
+cudaError_t launch_t(const SubtreeArgs &a, cudaStream_t s) {
+  const uint32_t T = 1u << a.t;
+  const uint32_t W = T >= 32 ? T / 32 : 1;
+  (void)W;
+  size_t smem = bit_words(a.t) * sizeof(uint32_t) + 2 * (size_t)T * sizeof(S);
+  auto kern = k_subtree<S, FK, SC, UH>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  StParams p{a.in,   a.in_stride, a.cls,      a.scale, a.mask, a.fv,
+             a.xhat, a.uhat,      a.w_stride, a.o,     a.t,    a.r};
+  kern<<<a.nframes, 32, smem, s>>>(p, a.in_is_llr);
+  return counted(cudaGetLastError(), 1);
+}
+
+template <typename S>
+cudaError_t launch_s(const SubtreeArgs &a, cudaStream_t s) {
+  const bool uh = a.uhat != nullptr;
+  if (a.fkind == 0) {
+    if (!a.shortcuts) return launch_t<S, 0, false, true>(a, s);
+    return uh ? launch_t<S, 0, true, true>(a, s) : launch_t<S, 0, true, false>(a, s);
+  }
+  if (!a.shortcuts) return launch_t<S, 1, false, true>(a, s);
+  return uh ? launch_t<S, 1, true, true>(a, s) : launch_t<S, 1, true, false>(a, s);
+}
+
+}  // namespace
+
+}  // namespace polar
