@@ -54,6 +54,8 @@ def parse():
                     help="served mixed stream: Poisson arrivals through the request server")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--inflight", type=int, default=48)
+    ap.add_argument("--subtree-log2", type=int, default=None,
+                    help="override the subtree size t (library default 13)")
     return ap.parse_args()
 
 
@@ -61,7 +63,8 @@ def config_of(w, args, extra=None):
     c = {"workload": w.name, "N": w.N, "log2n": w.log2n, "frames_per_gpu": w.frames,
          "channel": w.channel, "param": w.param, "rate": w.rate, "K": w.K,
          "fkind": args.fkind, "storage": args.prec, "parallelism": "replicas",
-         "l2": "flushed (256 MB write) between timed steps; LLR arrays exceed L2"}
+         "l2": "flushed (256 MB write) between timed steps; LLR arrays exceed L2",
+         "subtree_log2": args.subtree_log2 or 13}
     if extra:
         c.update(extra)
     return c
@@ -535,6 +538,9 @@ def run_serve(args):
 
 def main():
     args = parse()
+    if args.subtree_log2 is not None and args.impl == "ours":
+        from paper_1204_5882_gb300 import polar as P
+        P.polar_config_set("subtree_log2", args.subtree_log2)
     if args.impl == "reference":
         run_reference(args)
     elif args.serve:

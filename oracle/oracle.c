@@ -292,23 +292,36 @@ OR_API void or_bhatt_log_bsc(int n, double p, double *out)
     or_bhatt_log_from(n, lz0, out);
 }
 
-/* Chung-Richardson-Urbanke phi for the Gaussian approximation, in logs.   */
-/*   x < 10 : phiGA(x) = exp(-0.4527 x^0.86 + 0.0218)                       */
-/*   x >= 10: phiGA(x) = sqrt(pi/x) exp(-x/4) (1 - 10/(7x))                 */
+/* phi of the Gaussian approximation, in logs: the Chung-Richardson-Urbanke */
+/* form completed by a small-x piece so that phi(0) = 1 (the two-piece form */
+/* has phi(0) = e^0.0218 > 1, a fixed point of the minus step at m = 0.029, */
+/* and then rates the "minus^k plus^j" channels of long codes as reliable): */
+/*   x < 0.867      : phi(x) = exp(0.0564 x^2 - 0.48560 x)                  */
+/*   0.867 <= x < 10: phi(x) = exp(-0.4527 x^0.86 + 0.0218)                 */
+/*   x >= 10        : phi(x) = sqrt(pi/x) exp(-x/4) (1 - 10/(7x))           */
+/* The first two pieces meet at 0.867 (to the printed precision).           */
 OR_API double or_ga_lnphi(double x)
 {
+    if (x < 0.867) return 0.0564 * x * x - 0.48560 * x;
     if (x < 10.0) return -0.4527 * pow(x, 0.86) + 0.0218;
     return 0.5 * log(M_PI / x) - 0.25 * x + log1p(-10.0 / (7.0 * x));
 }
 
-/* Inverse of ln phiGA.  ln phiGA is decreasing on each piece but jumps up  */
-/* at x = 10 (left limit -3.2576, right value -3.2331), so targets inside   */
-/* the jump have one preimage on each piece.  Reading taken: the x < 10     */
-/* piece is used whenever its range contains t (closed-form inverse);       */
-/* otherwise the x >= 10 piece is inverted by bisection, doubling the       */
-/* bracket until it contains the root and halving until it cannot shrink.   */
+/* Inverse of ln phiGA.  Each piece is decreasing; at x = 10 the pieces do  */
+/* not meet (ln phi jumps up from -3.2576 to -3.2331), so targets inside    */
+/* that gap have two preimages.  Reading taken: the lowest piece whose      */
+/* range holds t is used -- the quadratic piece (smaller root, in the       */
+/* cancellation-free form -2t / (b + sqrt(b^2 + 4at))) when t is above its  */
+/* value at 0.867, else the middle piece in closed form when t is above its */
+/* limit at 10, else the x >= 10 piece by bisection (bracket doubled until  */
+/* it holds the root, then halved until it cannot shrink).                  */
 OR_API double or_ga_lnphi_inv(double t)
 {
+    double q867 = 0.0564 * 0.867 * 0.867 - 0.48560 * 0.867;
+    if (t > q867) {
+        if (t >= 0.0) return 0.0;
+        return -2.0 * t / (0.48560 + sqrt(0.48560 * 0.48560 + 4.0 * 0.0564 * t));
+    }
     double left10 = -0.4527 * pow(10.0, 0.86) + 0.0218;
     if (t > left10) {
         double v = (0.0218 - t) / 0.4527;

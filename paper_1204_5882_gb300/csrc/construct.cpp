@@ -29,9 +29,13 @@ static inline double bh_step(double lz, bool plus) {
 }
 
 // ---------------------------------------------------------------- GA
-// ln phi_GA(x): exp(-0.4527 x^0.86 + 0.0218) below 10, the asymptotic form
-// sqrt(pi/x) e^{-x/4} (1 - 10/(7x)) from 10 on.
+// ln phi_GA(x): Chung-Richardson-Urbanke phi completed by a small-x piece
+// so that phi(0) = 1 (without it the minus step has a fixed point at
+// m = 0.029 and long codes get "minus^k plus^j" channels rated reliable):
+//   exp(0.0564 x^2 - 0.48560 x) below 0.867, exp(-0.4527 x^0.86 + 0.0218)
+//   below 10, sqrt(pi/x) e^{-x/4} (1 - 10/(7x)) from 10 on.
 static inline double ga_lnphi(double x) {
+  if (x < 0.867) return 0.0564 * x * x - 0.48560 * x;
   if (x < 10.0) return -0.4527 * std::pow(x, 0.86) + 0.0218;
   return 0.5 * std::log(M_PI / x) - 0.25 * x + std::log1p(-10.0 / (7.0 * x));
 }
@@ -42,12 +46,19 @@ static inline double ga_dlnphi_hi(double x) {
   return -0.5 / x - 0.25 + (a / x) / (1.0 - a);
 }
 
-// Inverse of ln phi_GA.  The two pieces do not meet at x = 10 (ln phi jumps
-// up from -3.2576 to -3.2331), so targets in that gap have two preimages;
-// the x < 10 piece is taken whenever its range holds the target.  On the
-// x >= 10 piece the result is the smallest double x with ln phi(x) <= t,
-// found by Newton steps from x ~ -4t and finished by ulp steps.
+// Inverse of ln phi_GA.  The pieces are decreasing; at x = 10 they do not
+// meet (ln phi jumps up from -3.2576 to -3.2331), so targets in that gap have
+// two preimages.  The lowest piece whose range holds the target is used: the
+// quadratic piece (its smaller root, -2t / (b + sqrt(b^2 + 4at))) above its
+// value at 0.867, then the middle piece in closed form above its limit at
+// 10; on the x >= 10 piece the result is the smallest double x with
+// ln phi(x) <= t, found by Newton steps from x ~ -4t and finished by ulp steps.
 static double ga_lnphi_inv(double t) {
+  const double q867 = 0.0564 * 0.867 * 0.867 - 0.48560 * 0.867;
+  if (t > q867) {
+    if (t >= 0.0) return 0.0;
+    return -2.0 * t / (0.48560 + std::sqrt(0.48560 * 0.48560 + 4.0 * 0.0564 * t));
+  }
   const double left10 = -0.4527 * std::pow(10.0, 0.86) + 0.0218;
   if (t > left10) {
     double v = (0.0218 - t) / 0.4527;

@@ -101,6 +101,22 @@ def test_ga_phi_close_to_true_phi(m):
     assert math.exp(O.ga_lnphi(m)) == pytest.approx(_phi_true(m), rel=0.06)
 
 
+def test_ga_phi_is_one_at_zero_and_continuous_at_0867():
+    assert O.ga_lnphi(0.0) == 0.0
+    assert abs(math.exp(O.ga_lnphi(0.867 - 1e-12)) - math.exp(O.ga_lnphi(0.867))) < 1e-4
+    # slope at 0 close to the exact -1/2 (phi(m) = 1 - m/2 + O(m^2))
+    assert (math.exp(O.ga_lnphi(1e-4)) - 1.0) / 1e-4 == pytest.approx(-0.5, abs=0.02)
+
+
+def test_ga_minus_steps_tend_to_zero():
+    """Repeated minus steps drive m to 0 (a useless channel), as the true
+    density evolution does; a phi with phi(0) > 1 stalls at a positive m."""
+    m = O.ga_mean(16, 1.0)
+    assert m.min() < 1e-6
+    lp = O.ga_lnpe(16, 1.0)
+    assert lp[0] > math.log(0.49)            # the all-minus channel is a coin flip
+
+
 def test_ga_phi_nearly_continuous_at_10():
     assert abs(math.exp(O.ga_lnphi(10.0 - 1e-12)) - math.exp(O.ga_lnphi(10.0))) < 1e-2
 
