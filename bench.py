@@ -50,10 +50,19 @@ def parse():
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp16"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain per-frame baseline")
+    ap.add_argument("--no-n24", action="store_true",
+                    help="skip the extra 16 x 2^24 BI-AWGN measurement")
+    ap.add_argument("--plain-n24", action="store_true",
+                    help="also time one plain per-frame decode at 2^24 (several seconds)")
     ap.add_argument("--serve", action="store_true",
                     help="served mixed stream: Poisson arrivals through the request server")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--inflight", type=int, default=48)
+    ap.add_argument("--precision-sweep", action="store_true",
+                    help="FER of FP32/FP16/INT8 storage (min-sum and exact f) against the "
+                         "float64 exact-f oracle on the 2^22 precision workloads")
+    ap.add_argument("--sweep-frames", type=int, default=1000)
+    ap.add_argument("--oracle-frames", type=int, default=96)
     ap.add_argument("--subtree-log2", type=int, default=None,
                     help="override the subtree size t (library default 13)")
     return ap.parse_args()
@@ -210,6 +219,57 @@ def measured_peaks():
         return None
 
 
+def measure_n24(args, P, dev, steps=5, warmup=2):
+    """The 2^24 workload of the metric (16 frames, BI-AWGN sigma^2 = 1, R = 0.44),
+    inputs drawn on the device; same timing rules as the main measurement."""
+    import torch
+    w = S.WORKLOADS["biawgn_s1_n24"]
+    F, N = w.frames, w.N
+    fs = P.polar_build_frozen_set(w.log2n, w.channel, w.param, w.rate)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        xs, ys = zip(*[S.device_frame(w.channel, w.param, N, w.seed, f, dev) for f in range(F)])
+        xd, yd = torch.stack(xs), torch.stack(ys)
+        fv = torch.empty_like(xd)
+        P.polar_reveal(fs, F, xd, fv, stream)
+        llr = torch.empty(F, N, dtype=torch.float32, device=dev)
+        xh = torch.empty_like(xd)
+        flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+
+        def step():
+            P.polar_llr_from_channel(w.channel, w.param, yd, llr, stream)
+            P.polar_sc_decode_many(fs, F, llr, fv, xh, None, args.fkind, args.prec, stream)
+
+        for _ in range(warmup):
+            step()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        stream.synchronize()
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        stream.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        fer = float((xh != xd).any(dim=1).float().mean().item())
+        out = {"workload": w.name, "value": F * N / (ms / 1e3) / 1e6, "unit": UNIT,
+               "ms_per_step": ms, "steps": steps, "frames": F, "fer": fer,
+               "inputs": "drawn on the device (torch Philox, seeded per frame)"}
+        if args.plain_n24:
+            P.polar_config_set("plain", 1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            P.polar_sc_decode_many(fs, 1, llr, fv, xh, None, args.fkind, "fp32", stream)
+            b.record(stream)
+            stream.synchronize()
+            P.polar_config_set("plain", 0)
+            pms = a.elapsed_time(b)
+            out["plain_sc"] = {"value": N / (pms / 1e3) / 1e6, "unit": UNIT, "frames_timed": 1,
+                               "ms": pms}
+        return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -359,6 +419,10 @@ def run_ours(args):
                      "what": "one frame after another, float32 min-sum, no shortcuts, "
                              "no graphs, eager launches"}
 
+    extra_n24 = None
+    if rank == 0 and not args.no_n24:
+        extra_n24 = measure_n24(args, P, dev)
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -416,13 +480,13 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.prec == "fp32" else "f32 compute, f16 storage",
             "data": "synthetic", "config": config_of(w, args),
-            "roofline": roof, "roofline_streamed": hbm_roof(["stream_f", "stream_g"]),
+            "roofline": roof, "roofline_streamed": hbm_roof(["stream_f", "stream_g", "chain"]),
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": ck, "plain_sc": plain, "fer": fer,
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                            "p99": float(np.percentile(step_ms, 99)),
                            "what": "batch frames all complete at the end of their step"},
-            "kernel_time_ms": kernel_share}
+            "kernel_time_ms": kernel_share, "extra_n24": extra_n24}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -536,6 +600,94 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ precision sweep
+_PW = {}
+
+
+def _oracle64_init(channel, param, mask_bytes):
+    import oracle as O
+    O.lib()
+    _PW["ch"], _PW["param"] = channel, param
+    _PW["fz"] = np.frombuffer(mask_bytes, dtype=np.uint8)
+
+
+def _oracle64_frame(args):
+    """Frame error of the float64 exact-f oracle on one frame (x bits, y)."""
+    import oracle as O
+    xb, y = args
+    fz = _PW["fz"]
+    fv = O.reveal(xb, fz)
+    if _PW["ch"] == "bsc":
+        L = O.llr_bsc(y, _PW["param"], 64)
+    else:
+        L = O.llr_biawgn(y, _PW["param"], 64)
+    _, xh = O.sc_decode(L, fz, fv, "exact")
+    return int(not np.array_equal(xh, xb))
+
+
+def run_precision_sweep(args):
+    import torch
+
+    import oracle as O
+    from paper_1204_5882_gb300 import polar as P
+
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    O.build()
+    cases = [S.WORKLOADS["prec_biawgn_n22"], S.WORKLOADS["prec_bsc_n22"],
+             S.Workload("prec_bsc_n22_r070", "bsc", 0.02, 22, 0.70, 1000, 0x5EED + 7)]
+    out = {}
+    ctx = mp.get_context("spawn")
+    for w in cases:
+        F, N = args.sweep_frames, w.N
+        fs = P.polar_build_frozen_set(w.log2n, w.channel, w.param, w.rate)
+        ofz, _ = O.frozen_set(w.log2n, w.channel, w.param, w.rate)
+        errs = {}
+        oracle_inputs = []
+        batch = 50
+        for b0 in range(0, F, batch):
+            nb = min(batch, F - b0)
+            xs, ys = [], []
+            for i in range(b0, b0 + nb):
+                x, y = S.device_frame(w.channel, w.param, N, w.seed, i, dev)
+                xs.append(x)
+                ys.append(y)
+            xd, yd = torch.stack(xs), torch.stack(ys)
+            if b0 < args.oracle_frames:
+                for i in range(min(nb, args.oracle_frames - b0)):
+                    xb = S.unpack_bits(xd[i].cpu().numpy().view(np.uint32), N)
+                    yy = yd[i].cpu().numpy()
+                    yy = S.unpack_bits(yy.view(np.uint32), N) if w.channel == "bsc" else yy
+                    oracle_inputs.append((xb, yy))
+            fv = torch.empty_like(xd)
+            P.polar_reveal(fs, nb, xd, fv)
+            llr = torch.empty(nb, N, dtype=torch.float32, device=dev)
+            P.polar_llr_from_channel(w.channel, w.param, yd, llr)
+            xh = torch.empty_like(xd)
+            for fk in ("minsum", "exact"):
+                for prec in ("fp32", "fp16", "int8"):
+                    P.polar_sc_decode_many(fs, nb, llr, fv, xh, None, fk, prec)
+                    e = int((xh != xd).any(dim=1).sum().item())
+                    errs[(fk, prec)] = errs.get((fk, prec), 0) + e
+        with ctx.Pool(min(os.cpu_count() or 1, 64), initializer=_oracle64_init,
+                      initargs=(w.channel, w.param, ofz.tobytes())) as pool:
+            oerr = sum(pool.map(_oracle64_frame, oracle_inputs, chunksize=1))
+        no = len(oracle_inputs)
+        po = oerr / no
+        se_o = math.sqrt(max(po * (1 - po), 1.0 / no) / no)
+        res = {"oracle_fp64_exact": {"fer": po, "se": se_o, "frames": no}}
+        for (fk, prec), e in errs.items():
+            p_ = e / F
+            se = math.sqrt(max(p_ * (1 - p_), 1.0 / F) / F)
+            res[f"{prec}_{fk}"] = {"fer": p_, "se": se, "frames": F,
+                                   "penalty_vs_fp64": p_ - po,
+                                   "within_2se": abs(p_ - po) <= 2 * math.sqrt(se * se + se_o * se_o)}
+        out[w.name] = {"channel": w.channel, "param": w.param, "rate": w.rate, "N": N,
+                       "beta": w.rate / capacity_of(w.channel, w.param), "results": res}
+    print(json.dumps({"metric": "FER by storage precision vs float64 exact-f SC",
+                      "data": "synthetic", "sweep": out}), flush=True)
+
+
 def main():
     args = parse()
     if args.subtree_log2 is not None and args.impl == "ours":
@@ -545,6 +697,8 @@ def main():
         run_reference(args)
     elif args.serve:
         run_serve(args)
+    elif args.precision_sweep:
+        run_precision_sweep(args)
     else:
         run_ours(args)
 

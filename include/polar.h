@@ -78,6 +78,9 @@ const char *polar_last_error_string(void);
  *                   after another, no shortcuts, no graphs; 0 (default).
  *   "profile"       1 = time every kernel group with CUDA events (eager
  *                   launches, see polar_profile_read); 0 (default).
+ *   "fuse"          1 = each streamed f/g step and the f steps continuing it
+ *                   run as one fused column kernel (default); 0 = one launch
+ *                   per step.
  *   "int8_target"   INT8 storage: the per-frame scale is the power of two
  *                   2^rint(log2(target / mean|L|)) (mean in double over the
  *                   frame's channel LLRs); 1..64, default 8.
@@ -93,7 +96,8 @@ uint64_t polar_kernel_launches(void);
  * decode and map calls launch eagerly (no graphs) and bracket every kernel
  * group with CUDA events on the launching stream.  polar_profile_read
  * synchronises the recorded events and returns, for one kind ("llr",
- * "stream_f", "stream_g", "subtree", "rate0"), the summed device time in ms,
+ * "stream_f", "stream_g", "subtree", "rate0", "chain"), the summed device
+ * time in ms,
  * the number of launches and the algorithmic bytes those launches move
  * (inputs read once, outputs written once).  polar_profile_reset discards
  * what was recorded.  Any pointer may be NULL. */
@@ -171,10 +175,13 @@ int polar_reveal(const polar_frozen_set *fs, int nframes, const uint32_t *x_dev,
  *   uhat_dev         packed output u_hat, or NULL;
  *   fkind            min-sum f (bit-exact against a float32 recursive SC)
  *                    or exact f = 2 atanh(tanh(a/2) tanh(b/2));
- *   prec             storage precision of intermediate LLRs (FP16: round to
- *                    nearest even and saturate at +-65504; INT8: per-frame
- *                    power-of-two scale, round, saturate at +-127); every
- *                    f and g is computed in float32.
+ *   prec             storage precision of the LLRs kept in device memory:
+ *                    the channel LLRs as they are read and every level of
+ *                    the recursion above the on-chip subtree size 2^t (FP16:
+ *                    round to nearest even, saturate at +-65504; INT8: per-
+ *                    frame power-of-two scale, round, saturate at +-127).
+ *                    Levels below 2^t live in shared memory and registers in
+ *                    float32; every f and g is computed in float32.
  * Scratch: the library grows a per-stream workspace with cudaMalloc on the
  * first call that needs more (so that call must not be inside a stream
  * capture); about N * bytes(prec) per frame. */

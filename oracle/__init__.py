@@ -51,7 +51,8 @@ def lib():
         for nm in ("or_sc_decode_f64", "or_sc_decode_f32"):
             getattr(L, nm).argtypes = [C.c_int, C.c_int, P, P, P, P, P, P]
             getattr(L, nm).restype = C.c_int
-        L.or_sc_decode_store.argtypes = [C.c_int, C.c_int, C.c_int, C.c_float, P, P, P, P, P, P]
+        L.or_sc_decode_store.argtypes = [C.c_int, C.c_int, C.c_int, C.c_float, C.c_int, P, P, P,
+                                         P, P, P]
         L.or_sc_decode_store.restype = C.c_int
         L.or_int8_scale.argtypes = [P, C.c_size_t, C.c_double]
         L.or_int8_scale.restype = C.c_float
@@ -159,16 +160,18 @@ def int8_scale(llr, target: float = INT8_TARGET) -> float:
 
 
 def sc_decode_store(llr, frozen, fval, fkind: str = "minsum", store: str = "fp16",
-                    scale: float = 1.0, leaf: bool = False):
-    """SC with reduced-precision storage of every LLR (float arithmetic)."""
+                    scale: float = 1.0, leaf: bool = False, min_level: int = 0):
+    """SC with reduced-precision storage of the channel LLRs and of every
+    level k >= min_level (float arithmetic; lower levels stay float)."""
     llr = np.ascontiguousarray(llr, dtype=np.float32)
     n = log2_of(llr.size)
     fz, fv = _bits(frozen), _bits(fval)
     u = np.empty(llr.size, dtype=np.uint8)
     x = np.empty(llr.size, dtype=np.uint8)
     lf = np.empty(llr.size, dtype=np.float32) if leaf else None
-    rc = lib().or_sc_decode_store(n, FKIND[fkind], STORE[store], float(scale), _p(llr), _p(fz),
-                                  _p(fv), _p(u), _p(x), _p(lf) if leaf else None)
+    rc = lib().or_sc_decode_store(n, FKIND[fkind], STORE[store], float(scale), int(min_level),
+                                  _p(llr), _p(fz), _p(fv), _p(u), _p(x),
+                                  _p(lf) if leaf else None)
     if rc != 0:
         raise MemoryError("oracle decode failed")
     return (u, x, lf) if leaf else (u, x)

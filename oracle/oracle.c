@@ -176,9 +176,11 @@ OR_DEFINE_SC(float, f32, or_f_exact_f32, or_f_minsum_f32)
 
 /* ------------------------------------------------------------------------ */
 /* Reduced-precision storage of the LLRs (the paper's fixed-point decoder,  */
-/* Sec. 4, leaves the width open).  Reading: every LLR that is stored --    */
-/* the channel LLRs on entry and every f and g output -- is rounded to the  */
-/* storage format, while f and g themselves are evaluated in float:         */
+/* Sec. 4, leaves the width open).  Reading: the LLRs that are stored in    */
+/* bulk memory -- the channel LLRs on entry and every f and g output of the */
+/* levels k >= min_level (nodes of 2^k leaves) -- are rounded to the        */
+/* storage format; smaller nodes (min_level = the on-chip subtree size) and */
+/* all f and g arithmetic stay in float:                                    */
 /*   store 1 (half): clamp to +-65504, round to nearest even half;         */
 /*   store 2 (int8): values are L * scale (scale a power of two chosen per  */
 /*                   frame), rounded to nearest even integer, clamped to    */
@@ -198,13 +200,12 @@ static float q_store(float v, int store)
 static float f_store(float a, float b, int fkind, int store, float scale)
 {
     if (!fkind) return q_store(or_f_minsum_f32(a, b), store);
-    if (store == 2) return q_store(scale * or_f_exact_f32(a / scale, b / scale), store);
-    return q_store(or_f_exact_f32(a, b), store);
+    return q_store(scale * or_f_exact_f32(a / scale, b / scale), store);
 }
 
 static void sc_node_q(int k, const float *L, const uint8_t *frz, const uint8_t *fval,
                       uint8_t *u, uint8_t *beta, int fkind, int store, float scale,
-                      float *scratch, float *leaf)
+                      int min_level, float *scratch, float *leaf)
 {
     if (k == 0) {
         uint8_t d = frz[0] ? fval[0] : (uint8_t)(L[0] < 0.0f);
@@ -214,25 +215,27 @@ static void sc_node_q(int k, const float *L, const uint8_t *frz, const uint8_t *
         return;
     }
     size_t h = (size_t)1 << (k - 1);
+    int st = (k - 1 >= min_level) ? store : 0;   /* the children are stored? */
     float *Lc = scratch;
-    for (size_t j = 0; j < h; j++) Lc[j] = f_store(L[j], L[j + h], fkind, store, scale);
-    sc_node_q(k - 1, Lc, frz, fval, u, beta, fkind, store, scale, scratch + h, leaf);
+    for (size_t j = 0; j < h; j++) Lc[j] = f_store(L[j], L[j + h], fkind, st, scale);
+    sc_node_q(k - 1, Lc, frz, fval, u, beta, fkind, store, scale, min_level, scratch + h, leaf);
     for (size_t j = 0; j < h; j++)
-        Lc[j] = q_store(beta[j] ? (L[j + h] - L[j]) : (L[j + h] + L[j]), store);
-    sc_node_q(k - 1, Lc, frz + h, fval + h, u + h, beta + h, fkind, store, scale, scratch + h,
-              leaf ? leaf + h : NULL);
+        Lc[j] = q_store(beta[j] ? (L[j + h] - L[j]) : (L[j + h] + L[j]), st);
+    sc_node_q(k - 1, Lc, frz + h, fval + h, u + h, beta + h, fkind, store, scale, min_level,
+              scratch + h, leaf ? leaf + h : NULL);
     for (size_t j = 0; j < h; j++) beta[j] ^= beta[j + h];
 }
 
-OR_API int or_sc_decode_store(int n, int fkind, int store, float scale, const float *llr,
-                              const uint8_t *frozen, const uint8_t *fval, uint8_t *u_hat,
-                              uint8_t *x_hat, float *leaf)
+OR_API int or_sc_decode_store(int n, int fkind, int store, float scale, int min_level,
+                              const float *llr, const uint8_t *frozen, const uint8_t *fval,
+                              uint8_t *u_hat, uint8_t *x_hat, float *leaf)
 {
     size_t N = (size_t)1 << n;
     float *buf = (float *)malloc(sizeof(float) * 2 * N);
     if (!buf) return -1;
     for (size_t i = 0; i < N; i++) buf[i] = q_store(store == 2 ? llr[i] * scale : llr[i], store);
-    sc_node_q(n, buf, frozen, fval, u_hat, x_hat, fkind, store, scale, buf + N, leaf);
+    sc_node_q(n, buf, frozen, fval, u_hat, x_hat, fkind, store, scale, min_level, buf + N,
+              leaf);
     free(buf);
     return 0;
 }

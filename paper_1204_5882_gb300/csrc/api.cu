@@ -22,6 +22,7 @@ struct Config {
   std::atomic<long> plain{0};
   std::atomic<long> profile{0};
   std::atomic<long> int8_target{8};
+  std::atomic<long> fuse{1};
 };
 Config g_cfg;
 
@@ -31,8 +32,8 @@ struct ProfRec {
   cudaEvent_t a, b;
   double bytes;
 };
-const char *const kKinds[] = {"llr", "stream_f", "stream_g", "subtree", "rate0"};
-constexpr int kNumKinds = 5;
+const char *const kKinds[] = {"llr", "stream_f", "stream_g", "subtree", "rate0", "chain"};
+constexpr int kNumKinds = 6;
 std::mutex g_prof_mu;
 std::vector<ProfRec> g_prof_pending;
 double g_prof_ms[kNumKinds];
@@ -235,6 +236,22 @@ int run_ops(const Exec &x, cudaStream_t s, bool prof) {
         CK(launch_subtree(a, s));
         break;
       }
+      case OP_CHAIN: {
+        const int kt = op.k, kb = op.k - op.r;
+        const bool top = (kt == n);
+        const void *in = top ? static_cast<const void *>(g.llr) : level_ptr(x, kt);
+        const size_t ins = top ? N : (size_t(1) << kt);
+        const double inb = top ? 4.0 : sb;
+        double outb = 0;
+        for (int k = kb; k < kt; ++k) outb += double(uint64_t(1) << k) * sb;
+        ProfScope ps(prof, 5,
+                     F * (double(uint64_t(1) << kt) * inb + outb +
+                          (op.pad ? double(uint64_t(1) << (kt - 1)) / 8.0 : 0.0)),
+                     s);
+        CK(launch_chain(g.prec, g.fkind, op.pad != 0, in, ins, top, level_ptr(x, t), t,
+                        g.nframes, kt, kb, g.xhat, W, op.o, scale, s));
+        break;
+      }
       case OP_R0: {
         const size_t off = op.o >> 5, nw = size_t(1) << (op.k - 5);
         double cb = 0;
@@ -258,7 +275,7 @@ int current_device(int *dev) {
 }
 
 struct Opts {
-  bool plain, shortcuts, graphs, profile;
+  bool plain, shortcuts, graphs, profile, fuse;
   int subtree_log2;
 };
 
@@ -268,6 +285,7 @@ Opts current_opts() {
   o.shortcuts = !o.plain && g_cfg.shortcuts.load() != 0;
   o.graphs = !o.plain && g_cfg.graphs.load() != 0;
   o.profile = g_cfg.profile.load() != 0;
+  o.fuse = !o.plain && g_cfg.fuse.load() != 0;
   o.subtree_log2 = (int)g_cfg.subtree_log2.load();
   return o;
 }
@@ -285,7 +303,7 @@ int decode_group(const Group &g, cudaStream_t s, const Opts &opt) {
   cudaError_t e;
   const uint32_t *dmask = device_mask(fs, dev, &e);
   if (!dmask) return e == cudaErrorMemoryAllocation ? POLAR_ENOMEM : cuda_fail(e);
-  std::shared_ptr<Plan> plan = get_plan(fs, t, shortcuts);
+  std::shared_ptr<Plan> plan = get_plan(fs, t, shortcuts, opt.fuse);
   const uint32_t *dclass = nullptr;
   if (shortcuts && t >= 5) {
     dclass = device_class_table(fs, dev, t, &e);
@@ -405,7 +423,7 @@ int decode_with_scratch(const polar_frozen_set *fs_c, int nframes, const float *
   if (level_scratch_bytes(fs, nframes, prec, &t) > scratch_bytes) return POLAR_EINVAL;
   const bool shortcuts = g_cfg.shortcuts.load() != 0;
   if (shortcuts && t >= 5 && !dclass) return POLAR_EINVAL;
-  std::shared_ptr<Plan> plan = get_plan(fs, t, shortcuts);
+  std::shared_ptr<Plan> plan = get_plan(fs, t, shortcuts, g_cfg.fuse.load() != 0);
   Exec x{plan.get(), &g, dmask, scratch, (int)fs->log2n, t, shortcuts && t >= 5 ? dclass : nullptr};
   return run_ops(x, s, false);
 }
@@ -473,6 +491,8 @@ int polar_config_set(const char *key, long value) {
     g_cfg.plain = value ? 1 : 0;
   } else if (!strcmp(key, "profile")) {
     g_cfg.profile = value ? 1 : 0;
+  } else if (!strcmp(key, "fuse")) {
+    g_cfg.fuse = value ? 1 : 0;
   } else if (!strcmp(key, "int8_target")) {
     if (value < 1 || value > 64) return POLAR_EINVAL;
     g_cfg.int8_target = value;
@@ -490,6 +510,7 @@ int polar_config_get(const char *key, long *value) {
   else if (!strcmp(key, "plain")) *value = g_cfg.plain;
   else if (!strcmp(key, "profile")) *value = g_cfg.profile;
   else if (!strcmp(key, "int8_target")) *value = g_cfg.int8_target;
+  else if (!strcmp(key, "fuse")) *value = g_cfg.fuse;
   else return POLAR_ENOTFOUND;
   return POLAR_OK;
 }

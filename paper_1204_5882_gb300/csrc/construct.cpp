@@ -256,20 +256,49 @@ static void plan_visit(const polar_frozen_set *fs, Plan &p, int k, uint64_t o) {
     p.n_f++;
   }
   plan_visit(fs, p, k - 1, o);
-  p.ops.push_back(Op{OP_G, (uint8_t)k, 0, 0, o});
-  p.n_g++;
+  if (!rate0(k - 1, o + h)) {          // a rate-0 right child needs no LLRs
+    p.ops.push_back(Op{OP_G, (uint8_t)k, 0, 0, o});
+    p.n_g++;
+  }
   plan_visit(fs, p, k - 1, o + h);
 }
 
-std::shared_ptr<Plan> get_plan(polar_frozen_set *fs, int t, bool shortcuts) {
+// Merge each f or g step with the f steps that directly continue it (level
+// by level down the left edge) into one fused chain of at most 7 levels.
+static void plan_fuse(Plan &p) {
+  std::vector<Op> out;
+  out.reserve(p.ops.size());
+  for (size_t i = 0; i < p.ops.size();) {
+    const Op &a = p.ops[i];
+    if (a.kind != OP_F && a.kind != OP_G) {
+      out.push_back(a);
+      ++i;
+      continue;
+    }
+    size_t j = i + 1;
+    int levels = 1;
+    while (j < p.ops.size() && levels < 7 && p.ops[j].kind == OP_F &&
+           p.ops[j].k == a.k - levels) {
+      ++levels;
+      ++j;
+    }
+    out.push_back(Op{OP_CHAIN, a.k, (uint8_t)levels, (uint8_t)(a.kind == OP_G ? 1 : 0), a.o});
+    p.n_chain++;
+    i = j;
+  }
+  p.ops.swap(out);
+}
+
+std::shared_ptr<Plan> get_plan(polar_frozen_set *fs, int t, bool shortcuts, bool fuse) {
   std::lock_guard<std::mutex> g(fs->mu);
-  auto key = std::make_pair(t, shortcuts ? 1 : 0);
+  auto key = std::make_pair(t, (shortcuts ? 1 : 0) | (fuse ? 2 : 0));
   auto it = fs->plans.find(key);
   if (it != fs->plans.end()) return it->second;
   auto p = std::make_shared<Plan>();
   p->t = t;
   p->shortcuts = shortcuts;
   plan_visit(fs, *p, (int)fs->log2n, 0);
+  if (fuse) plan_fuse(*p);
   fs->plans[key] = p;
   return p;
 }

@@ -17,12 +17,17 @@ __device__ __forceinline__ float f_minsum(float a, float b) {
 
 // Exact check-node update f = 2 atanh(tanh(a/2) tanh(b/2)) (Sec. 4's update
 // through phi), evaluated as
-//   sgn(a) sgn(b) [min(A,B) + log1p(e^{-(A+B)}) - log1p(e^{-|A-B|})]
-// which never forms atanh(+-1); the magnitude is clamped at zero because
-// rounding can push it slightly negative for tiny inputs.
+//   sgn(a) sgn(b) [min(A,B) + c(A+B) - c(|A-B|)],  c(d) = ln(1 + e^-d),
+// which never forms atanh(+-1).  c is taken with the SFU exponential and
+// logarithm (absolute error ~1e-7, far below any LLR that decides a bit);
+// the magnitude is clamped at zero because rounding can push it slightly
+// negative for tiny inputs.  Exact f is compared with the float64 oracle
+// statistically (frame error rate), never bit for bit.
+__device__ __forceinline__ float corr_c(float d) { return __logf(1.0f + __expf(-d)); }
+
 __device__ __forceinline__ float f_exact(float a, float b) {
   float A = fabsf(a), B = fabsf(b);
-  float m = fminf(A, B) + log1pf(expf(-(A + B))) - log1pf(expf(-fabsf(A - B)));
+  float m = fminf(A, B) + corr_c(A + B) - corr_c(fabsf(A - B));
   m = fmaxf(m, 0.0f);
   uint32_t s = (__float_as_uint(a) ^ __float_as_uint(b)) & 0x80000000u;
   return __uint_as_float(__float_as_uint(m) | s);
@@ -90,6 +95,15 @@ __device__ __forceinline__ float f_st(float a, float b, float s) {
   if (FK == 0) return f_minsum(a, b);
   if (sizeof(S) == 1) return s * f_exact(a / s, b / s);
   return f_exact(a, b);
+}
+
+// f on values that may carry a per-frame scale s (int8 storage: values are
+// L * s; s = 1 otherwise): min-sum commutes with the scale, exact f is taken
+// on L.  With s = 1 both are bit-identical to f_op.
+template <int FK>
+__device__ __forceinline__ float f_scaled(float a, float b, float s) {
+  if (FK == 0) return f_minsum(a, b);
+  return s * f_exact(a / s, b / s);
 }
 
 // ---------------------------------------------------------------- bits

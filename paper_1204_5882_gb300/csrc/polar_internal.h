@@ -28,13 +28,14 @@ enum OpKind : uint8_t {
   OP_G = 1,   // level k -> k-1, right child LLRs L'[j] = g(L[j], L[j+h], b[o+j])
   OP_ST = 2,  // decode the subtree of 2^t leaves at o in one CTA
   OP_R0 = 3,  // rate-0 node of 2^k leaves at o: partial sums = fv F^{(x)k}
+  OP_CHAIN = 4,  // fused steps level k -> k - r: first g (pad = 1) or f, then f
 };
 
 struct Op {
   uint8_t kind;
   uint8_t k;
   uint8_t r;   // partial-sum combine levels done after a unit (ST / R0)
-  uint8_t pad;
+  uint8_t pad;   // OP_CHAIN: 1 = the first step is g
   uint64_t o;
 };
 
@@ -42,7 +43,7 @@ struct Plan {
   int t = 0;
   bool shortcuts = true;
   std::vector<Op> ops;
-  int n_st = 0, n_f = 0, n_g = 0, n_r0 = 0;
+  int n_st = 0, n_f = 0, n_g = 0, n_r0 = 0, n_chain = 0;
 };
 
 }  // namespace polar
@@ -57,7 +58,7 @@ struct polar_frozen_set {
   std::map<int, uint32_t *> dmask;                        // device -> mask copy
   std::map<std::pair<int, int>, uint32_t *> dclass;       // (device, t) -> class table
   std::map<int, std::shared_ptr<std::vector<uint32_t>>> hclass;   // t -> host class table
-  std::map<std::pair<int, int>, std::shared_ptr<polar::Plan>> plans;  // (t, shortcuts)
+  std::map<std::pair<int, int>, std::shared_ptr<polar::Plan>> plans;  // (t, flags)
 };
 
 namespace polar {
@@ -67,7 +68,7 @@ int build_frozen_set(uint32_t log2n, polar_channel ch, double param, double rate
                      polar_frozen_set **out);
 int frozen_set_from_mask(uint32_t log2n, const uint32_t *mask, polar_frozen_set **out);
 NodeClass node_class_host(const polar_frozen_set *fs, int k, uint64_t o);
-std::shared_ptr<Plan> get_plan(polar_frozen_set *fs, int t, bool shortcuts);
+std::shared_ptr<Plan> get_plan(polar_frozen_set *fs, int t, bool shortcuts, bool fuse);
 const uint32_t *device_mask(polar_frozen_set *fs, int device, cudaError_t *err);
 // Node-class table of every subtree of 2^t leaves (levels 5..t): per subtree
 // class_words(t) words of "rate 0" bits then as many of "rate 1" bits; node
@@ -102,6 +103,13 @@ cudaError_t launch_stream_g(int prec, const void *in, size_t in_stride, bool in_
                             void *out, size_t out_stride, uint64_t h,
                             const uint32_t *xhat, size_t xhat_stride_w, uint64_t o,
                             int nframes, const float *scale, cudaStream_t s);
+// Fused run of streamed steps kt -> kb (first step g if first_g, then f);
+// lv_base = start of the level buffers (level k of frame f at
+// F * (2^k - 2^t) + f * 2^k elements).  kt - kb <= 7.
+cudaError_t launch_chain(int prec, int fkind, bool first_g, const void *in, size_t in_stride,
+                         bool in_is_llr, void *lv_base, int t, int nframes, int kt, int kb,
+                         const uint32_t *xhat, size_t xhat_stride_w, uint64_t o_left,
+                         const float *scale, cudaStream_t s);
 // Per-frame int8 scale 2^round(log2(target / mean|L|)) (1 if all L = 0).
 cudaError_t launch_int8_scale(const float *llr, size_t n, int nframes, double target,
                               float *scale, cudaStream_t s);

@@ -305,6 +305,202 @@ static cudaError_t stream_g_t(const void *in, size_t in_stride, bool in_is_llr, 
   return counted(cudaGetLastError(), 1);
 }
 
+// ---------------------------------------------------------------- fused chains
+// One launch for a run of the recursion's streamed steps: level kt -> kt-1 by
+// f (left child) or g (right child, partial sums of the left sibling read
+// from x_hat), then f down to level kb.  The work is split in columns: column
+// c of a frame holds, at every level k in kb..kt, the elements whose index
+// modulo 2^kb lies in [c*B, c*B + B); f and g pair index j with j + 2^(k-1),
+// which stays inside the column, so a CTA runs all levels of its column in
+// shared memory and writes each level once (no re-reads, one launch).
+// Stored values are rounded to Tout before the next level uses them.
+// Four consecutive values of a storage type, widened to / narrowed from float.
+template <typename T>
+struct Quad;
+template <>
+struct Quad<float> {
+  static __device__ __forceinline__ float4 ld(const float *p) {
+    return *reinterpret_cast<const float4 *>(p);
+  }
+  static __device__ __forceinline__ void st(float *p, float4 v) {
+    *reinterpret_cast<float4 *>(p) = v;
+  }
+};
+template <>
+struct Quad<__half> {
+  static __device__ __forceinline__ float4 ld(const __half *p) {
+    const uint2 u = *reinterpret_cast<const uint2 *>(p);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+  }
+  static __device__ __forceinline__ void st(__half *p, float4 v) {   // v already rounded
+    __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+    uint2 u;
+    u.x = *reinterpret_cast<uint32_t *>(&a);
+    u.y = *reinterpret_cast<uint32_t *>(&b);
+    *reinterpret_cast<uint2 *>(p) = u;
+  }
+};
+template <>
+struct Quad<int8_t> {
+  static __device__ __forceinline__ float4 ld(const int8_t *p) {
+    const char4 c = *reinterpret_cast<const char4 *>(p);
+    return make_float4((float)c.x, (float)c.y, (float)c.z, (float)c.w);
+  }
+  static __device__ __forceinline__ void st(int8_t *p, float4 v) {   // v already rounded
+    *reinterpret_cast<char4 *>(p) =
+        make_char4((signed char)v.x, (signed char)v.y, (signed char)v.z, (signed char)v.w);
+  }
+};
+
+template <typename Tin, typename Tout>
+__device__ __forceinline__ float4 load4_in(const Tin *p, float sc) {
+  float4 v = Quad<Tin>::ld(p);
+  if constexpr (sizeof(Tin) == 4 && sizeof(Tout) != 4) {
+    v.x = rnd<Tout>(v.x * sc);
+    v.y = rnd<Tout>(v.y * sc);
+    v.z = rnd<Tout>(v.z * sc);
+    v.w = rnd<Tout>(v.w * sc);
+  }
+  return v;
+}
+
+// One launch for a run of the recursion's streamed steps: level kt -> kt-1 by
+// f (left child) or g (right child, partial sums of the left sibling read
+// from x_hat), then f down to level kb.  The work is split in columns: column
+// c of a frame holds, at every level k in kb..kt, the elements whose index
+// modulo 2^kb lies in [c*B, c*B + B); f and g pair index j with j + 2^(k-1),
+// which stays inside the column, so a CTA runs all levels of its column in
+// shared memory and writes each level once (no re-reads, one launch).
+// Threads work on four consecutive elements; stored values are rounded to
+// Tout before the next level uses them.
+template <typename Tin, typename Tout, int FK, bool FIRST_G>
+__global__ void __launch_bounds__(256) k_chain(const Tin *__restrict__ in, size_t in_stride,
+                                               Tout *__restrict__ lv_base, int t, int nframes,
+                                               int kt, int kb, int logB,
+                                               const uint32_t *__restrict__ xhat,
+                                               size_t x_stride, uint64_t o_left,
+                                               const float *__restrict__ scale) {
+  extern __shared__ float4 cs4[];
+  const int cols = 1 << (kb - logB);
+  const int f = blockIdx.x >> (kb - logB), c = blockIdx.x & (cols - 1);
+  const float sc = scale ? scale[f] : 1.0f;
+  const Tin *src = in + (size_t)f * in_stride;
+  const uint32_t qB = (1u << logB) >> 2;                  // quads per row
+  const int lq = logB - 2;
+  const uint32_t nin = qB << (kt - kb);
+  const uint64_t col0 = (uint64_t)c << logB;
+  for (uint32_t b = threadIdx.x; b < nin; b += blockDim.x * 4) {
+    float4 q[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const uint32_t e = b + r * blockDim.x;
+      if (e < nin) {
+        const uint64_t j = ((uint64_t)(e >> lq) << kb) + col0 + ((e & (qB - 1)) << 2);
+        q[r] = load4_in<Tin, Tout>(src + j, sc);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const uint32_t e = b + r * blockDim.x;
+      if (e < nin) cs4[e] = q[r];
+    }
+  }
+  __syncthreads();
+  const uint32_t *beta = FIRST_G ? xhat + (size_t)f * x_stride : nullptr;
+  for (int k = kt; k > kb; --k) {
+    const uint32_t half = qB << (k - 1 - kb);             // quads of level k-1
+    Tout *dst = lv_base + (size_t)nframes * ((size_t(1) << (k - 1)) - (size_t(1) << t)) +
+                (size_t)f * (size_t(1) << (k - 1));
+    for (uint32_t e = threadIdx.x; e < half; e += blockDim.x) {
+      const float4 a = cs4[e], bq = cs4[e + half];
+      const uint64_t j = ((uint64_t)(e >> lq) << kb) + col0 + ((e & (qB - 1)) << 2);
+      float4 v;
+      if (FIRST_G && k == kt) {
+        const uint64_t pos = o_left + j;
+        const uint32_t bits = (beta[pos >> 5] >> (pos & 31)) & 0xFu;
+        v.x = g_op(a.x, bq.x, bits & 1u);
+        v.y = g_op(a.y, bq.y, bits & 2u);
+        v.z = g_op(a.z, bq.z, bits & 4u);
+        v.w = g_op(a.w, bq.w, bits & 8u);
+      } else {
+        v.x = f_st<Tout, FK>(a.x, bq.x, sc);
+        v.y = f_st<Tout, FK>(a.y, bq.y, sc);
+        v.z = f_st<Tout, FK>(a.z, bq.z, sc);
+        v.w = f_st<Tout, FK>(a.w, bq.w, sc);
+      }
+      v.x = rnd<Tout>(v.x);
+      v.y = rnd<Tout>(v.y);
+      v.z = rnd<Tout>(v.z);
+      v.w = rnd<Tout>(v.w);
+      Quad<Tout>::st(dst + j, v);
+      cs4[e] = v;                      // in place: quad e is read by this thread only
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int FK, bool G>
+static cudaError_t chain_t(const void *in, size_t in_stride, bool in_is_llr, void *lv_base, int t,
+                           int nframes, int kt, int kb, const uint32_t *xhat, size_t xs,
+                           uint64_t o, const float *scale, cudaStream_t s) {
+  // Row width 2^logB: about a thousand CTAs over the batch, at most 64 KB of
+  // float column per CTA, at least 32 elements per row.
+  int want = 0;
+  while ((nframes << want) < 1024) ++want;                  // columns per frame, log2
+  int logB = kb - want;
+  if (logB > 14 - (kt - kb)) logB = 14 - (kt - kb);
+  if (logB < 5) logB = 5;
+  if (logB > kb) logB = kb;
+  const size_t smem = (size_t(1) << (logB + kt - kb)) * sizeof(float);
+  const unsigned grid = (unsigned)nframes << (kb - logB);
+  if (in_is_llr) {
+    auto kern = k_chain<float, T, FK, G>;
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<grid, 256, smem, s>>>((const float *)in, in_stride, (T *)lv_base, t, nframes, kt, kb,
+                                 logB, xhat, xs, o, scale);
+  } else {
+    auto kern = k_chain<T, T, FK, G>;
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<grid, 256, smem, s>>>((const T *)in, in_stride, (T *)lv_base, t, nframes, kt, kb,
+                                 logB, xhat, xs, o, scale);
+  }
+  return counted(cudaGetLastError(), 1);
+}
+
+template <typename T>
+static cudaError_t chain_p(int fkind, bool first_g, const void *in, size_t in_stride,
+                           bool in_is_llr, void *lv_base, int t, int nframes, int kt, int kb,
+                           const uint32_t *xhat, size_t xs, uint64_t o, const float *scale,
+                           cudaStream_t s) {
+  if (fkind == 0)
+    return first_g ? chain_t<T, 0, true>(in, in_stride, in_is_llr, lv_base, t, nframes, kt, kb,
+                                         xhat, xs, o, scale, s)
+                   : chain_t<T, 0, false>(in, in_stride, in_is_llr, lv_base, t, nframes, kt, kb,
+                                          xhat, xs, o, scale, s);
+  return first_g ? chain_t<T, 1, true>(in, in_stride, in_is_llr, lv_base, t, nframes, kt, kb,
+                                       xhat, xs, o, scale, s)
+                 : chain_t<T, 1, false>(in, in_stride, in_is_llr, lv_base, t, nframes, kt, kb,
+                                        xhat, xs, o, scale, s);
+}
+
+cudaError_t launch_chain(int prec, int fkind, bool first_g, const void *in, size_t in_stride,
+                         bool in_is_llr, void *lv_base, int t, int nframes, int kt, int kb,
+                         const uint32_t *xhat, size_t xhat_stride_w, uint64_t o_left,
+                         const float *scale, cudaStream_t s) {
+  if (prec == POLAR_FP16)
+    return chain_p<__half>(fkind, first_g, in, in_stride, in_is_llr, lv_base, t, nframes, kt, kb,
+                           xhat, xhat_stride_w, o_left, scale, s);
+  if (prec == POLAR_INT8)
+    return chain_p<int8_t>(fkind, first_g, in, in_stride, in_is_llr, lv_base, t, nframes, kt,
+                           kb, xhat, xhat_stride_w, o_left, scale, s);
+  return chain_p<float>(fkind, first_g, in, in_stride, in_is_llr, lv_base, t, nframes, kt, kb,
+                        xhat, xhat_stride_w, o_left, scale, s);
+}
+
 // ---------------------------------------------------------------- int8 scale
 // One CTA per frame: mean |L| in double (fixed reduction tree), then
 // s = 2^rint(log2(target / mean)), clamped to 2^+-100; s = 1 if every L = 0.

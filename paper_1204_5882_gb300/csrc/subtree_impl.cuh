@@ -108,7 +108,7 @@ struct Dec {
       bL = encode_word(fvL, K - 1);
     } else {
 #pragma unroll
-      for (int j = 0; j < H; ++j) l[j] = rnd<S>(f_st<S, FK>(a[j], a[j + H], sc));
+      for (int j = 0; j < H; ++j) l[j] = rnd<S>(f_scaled<FK>(a[j], a[j + H], sc));
       bL = Dec<K - 1, FK, true, S>::run(l, fzL, fvL, uL, sc);
     }
 #pragma unroll
@@ -225,7 +225,7 @@ struct Tile {
           if (!(r & hw)) bL[r] ^= bL[r + hw];
     } else {
 #pragma unroll
-      for (int r = 0; r < H; ++r) c[r] = rnd<S>(f_st<S, FK>(v[r], v[r + H], sc));
+      for (int r = 0; r < H; ++r) c[r] = rnd<S>(f_scaled<FK>(v[r], v[r + H], sc));
       Tile<K - 1, FK, S, UH>::run(c, m, fv, bL, uL, sc, gbuf, lane);
     }
     const int sh = 31 - lane;
@@ -475,11 +475,11 @@ struct Warp {
           y[q] = Store<S>::ld(a + h + i + 32 * q);
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) Store<S>::st(c + i + 32 * q, f_st<S, FK>(x[q], y[q], sc));
+        for (int q = 0; q < 4; ++q) Store<S>::st(c + i + 32 * q, f_scaled<FK>(x[q], y[q], sc));
       }
     } else {
       for (uint32_t i = lane; i < h; i += 32)
-        Store<S>::st(c + i, f_st<S, FK>(Store<S>::ld(a + i), Store<S>::ld(a + h + i), sc));
+        Store<S>::st(c + i, f_scaled<FK>(Store<S>::ld(a + i), Store<S>::ld(a + h + i), sc));
     }
     __syncwarp();
   }
@@ -537,8 +537,11 @@ __host__ __device__ inline uint32_t bit_words(int t) {
   return ((4 * W + 2 * CW + 3u) & ~3u) + 32u;
 }
 
-template <typename S, int FK, bool SC, bool UH>
+// Tin: storage of the level-t input (the streamed levels); inside the CTA
+// every level is float.
+template <typename Tin, int FK, bool SC, bool UH>
 __global__ void __launch_bounds__(32) k_subtree(StParams p, bool in_is_llr) {
+  using S = float;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int t = p.t;
   const uint32_t T = 1u << t;
@@ -589,21 +592,22 @@ __global__ void __launch_bounds__(32) k_subtree(StParams p, bool in_is_llr) {
         for (int r = 0; r < 8; ++r) {
           const uint32_t i = b + 32 * r + lane;
           if (i < T / 4) {
-            Store<S>::st(Lt + 4 * i, q[r].x * w.sc);
-            Store<S>::st(Lt + 4 * i + 1, q[r].y * w.sc);
-            Store<S>::st(Lt + 4 * i + 2, q[r].z * w.sc);
-            Store<S>::st(Lt + 4 * i + 3, q[r].w * w.sc);
+            Lt[4 * i] = rnd<Tin>(q[r].x * w.sc);
+            Lt[4 * i + 1] = rnd<Tin>(q[r].y * w.sc);
+            Lt[4 * i + 2] = rnd<Tin>(q[r].z * w.sc);
+            Lt[4 * i + 3] = rnd<Tin>(q[r].w * w.sc);
           }
         }
       }
     } else {
-      for (uint32_t i = lane; i < T; i += 32) Store<S>::st(Lt + i, src[i] * w.sc);
+      for (uint32_t i = lane; i < T; i += 32) Lt[i] = rnd<Tin>(src[i] * w.sc);
     }
   } else {
-    const S *src = reinterpret_cast<const S *>(p.in) + fr * p.in_stride;
-    const uint32_t n16 = (uint32_t)(T * sizeof(S) / 16);   // T * sizeof(S) >= 32 here
+    // Tin-typed level t (16-byte chunks of 4, 8 or 16 values), widened to float
+    const Tin *src = reinterpret_cast<const Tin *>(p.in) + fr * p.in_stride;
+    constexpr uint32_t PER = 16 / sizeof(Tin);
+    const uint32_t n16 = T / PER;                            // T >= 32 here
     const uint4 *s16 = reinterpret_cast<const uint4 *>(src);
-    uint4 *d16 = reinterpret_cast<uint4 *>(Lt);
     for (uint32_t b = 0; b < n16; b += 32 * 8) {
       uint4 q[8];
 #pragma unroll
@@ -614,7 +618,11 @@ __global__ void __launch_bounds__(32) k_subtree(StParams p, bool in_is_llr) {
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
         const uint32_t i = b + 32 * r + lane;
-        if (i < n16) d16[i] = q[r];
+        if (i < n16) {
+          const Tin *e = reinterpret_cast<const Tin *>(&q[r]);
+#pragma unroll
+          for (uint32_t c = 0; c < PER; ++c) Lt[PER * i + c] = Store<Tin>::ld(e + c);
+        }
       }
     }
   }
@@ -676,13 +684,14 @@ __global__ void __launch_bounds__(32) k_subtree(StParams p, bool in_is_llr) {
   if (p.r > 0) cascade_device(p.xhat + fr * p.w_stride, t, p.o, p.r);
 }
 
-template <typename S, int FK, bool SC, bool UH>
+template <typename Tin, int FK, bool SC, bool UH>
 cudaError_t launch_t(const SubtreeArgs &a, cudaStream_t s) {
+  using S = float;
   const uint32_t T = 1u << a.t;
   const uint32_t W = T >= 32 ? T / 32 : 1;
   (void)W;
   size_t smem = bit_words(a.t) * sizeof(uint32_t) + 2 * (size_t)T * sizeof(S);
-  auto kern = k_subtree<S, FK, SC, UH>;
+  auto kern = k_subtree<Tin, FK, SC, UH>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);

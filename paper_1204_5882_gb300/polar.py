@@ -153,7 +153,7 @@ def polar_profile_reset():
     _lib.polar_profile_reset()
 
 
-PROFILE_KINDS = ("llr", "stream_f", "stream_g", "subtree", "rate0")
+PROFILE_KINDS = ("llr", "stream_f", "stream_g", "subtree", "rate0", "chain")
 
 
 # ------------------------------------------------------------------ frozen sets

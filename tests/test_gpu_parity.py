@@ -41,7 +41,8 @@ def words_np(t):
 
 @pytest.fixture(autouse=True)
 def default_config(P):
-    saved = {k: P.polar_config_get(k) for k in ("subtree_log2", "shortcuts", "graphs", "plain")}
+    saved = {k: P.polar_config_get(k)
+             for k in ("subtree_log2", "shortcuts", "graphs", "plain", "fuse")}
     yield
     for k, v in saved.items():
         P.polar_config_set(k, v)
@@ -149,9 +150,11 @@ def test_minsum_bitexact_small(P, n, kind, t):
     check_minsum(P, n, kind, F=2, seed=1000 * n + t + 7, llr_kind="bsc")
 
 
-@pytest.mark.parametrize("mode", ["no_shortcuts", "no_graphs", "plain"])
+@pytest.mark.parametrize("mode", ["no_shortcuts", "no_graphs", "plain", "no_fuse"])
 def test_minsum_bitexact_modes(P, mode):
-    if mode == "no_shortcuts":
+    if mode == "no_fuse":
+        P.polar_config_set("fuse", 0)
+    elif mode == "no_shortcuts":
         P.polar_config_set("shortcuts", 0)
     elif mode == "no_graphs":
         P.polar_config_set("graphs", 0)
@@ -259,9 +262,10 @@ def check_store(P, n, kind, F, seed, prec, llr_kind="gauss"):
     fvb = (rng.integers(0, 2, (F, N)) * fz).astype(np.uint8)
     fvw = np.stack([S.pack_bits(r) for r in fvb])
     xh, uh = gpu_decode(P, fs, L, fvw, "minsum", prec)
+    t = min(n, P.polar_config_get("subtree_log2"))      # levels below t stay on chip in float
     for f in range(F):
         sc = O.int8_scale(L[f], P.polar_config_get("int8_target")) if prec == "int8" else 1.0
-        ou, ox = O.sc_decode_store(L[f], fz, fvb[f], "minsum", prec, sc)
+        ou, ox = O.sc_decode_store(L[f], fz, fvb[f], "minsum", prec, sc, min_level=t)
         assert np.array_equal(S.unpack_bits(xh[f], N), ox), (n, kind, prec, f)
         assert np.array_equal(S.unpack_bits(uh[f], N), ou), (n, kind, prec, f)
 
@@ -270,8 +274,9 @@ def check_store(P, n, kind, F, seed, prec, llr_kind="gauss"):
 @pytest.mark.parametrize("t", [5, 9, 13])
 @pytest.mark.parametrize("n", [3, 5, 8, 12, 15])
 def test_reduced_storage_minsum_bitexact(P, prec, t, n):
-    """FP16 / INT8 storage: every stored LLR rounded (and saturated) exactly as
-    the oracle's storage model does, so min-sum decisions match bit for bit."""
+    """FP16 / INT8 storage: every LLR stored in bulk memory (the channel LLRs on
+    entry and the levels >= t) is rounded and saturated exactly as the
+    oracle's storage model does, so min-sum decisions match bit for bit."""
     P.polar_config_set("subtree_log2", t)
     check_store(P, n, "polar", 3, 500 + n + t, prec, "gauss")
     check_store(P, n, "random", 2, 600 + n + t, prec, "bsc")
@@ -286,5 +291,6 @@ def test_reduced_storage_workload_bitexact(P, prec):
         L = O.llr_bsc(S.unpack_bits(y[f], w.N), w.param, 32)
         fv = O.reveal(S.unpack_bits(x[f], w.N), ofz)
         sc = O.int8_scale(L, P.polar_config_get("int8_target")) if prec == "int8" else 1.0
-        ou, ox = O.sc_decode_store(L, ofz, fv, "minsum", prec, sc)
+        t = min(w.log2n, P.polar_config_get("subtree_log2"))
+        ou, ox = O.sc_decode_store(L, ofz, fv, "minsum", prec, sc, min_level=t)
         assert np.array_equal(S.unpack_bits(xh[f], w.N), ox), f
