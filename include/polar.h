@@ -231,6 +231,8 @@ typedef struct {
     size_t mem_budget;  /* bytes of decode scratch all slots may hold together */
     polar_fkind fkind;
     polar_prec prec;
+    int threads;        /* host scheduler threads launching work, 0 = 4; each owns
+                           an equal share of the slots (launch cost is on the host) */
 } polar_server_config;
 
 typedef struct {

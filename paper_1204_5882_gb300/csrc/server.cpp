@@ -1,8 +1,10 @@
 // Request server: continuous batching of reconciliation frames.
 //
 // Requests (one or more contiguous frames sharing a frozen set) enter a
-// bounded host queue.  A scheduler thread owns a pool of decode slots, each a
-// non-blocking CUDA stream with its own scratch workspace.  Whenever a slot
+// bounded host queue.  Scheduler threads (each owning an equal share of the
+// decode slots, so that the host cost of launching is spread over cores)
+// serve it; a slot is a non-blocking CUDA stream with its own scratch
+// workspace.  Whenever a slot
 // is free and the server's scratch budget allows the request's workspace, the
 // oldest pending request is launched on that slot; completion is detected
 // with a CUDA event and reported through poll / wait.  Requests submitted
@@ -54,7 +56,7 @@ struct polar_server {
   std::unordered_map<uint64_t, Record> records;
   std::mutex mu;
   std::condition_variable cv_done;
-  std::thread thread;
+  std::vector<std::thread> threads;
   bool stop = false;
   uint64_t next_ticket = 1;
   size_t ws_total = 0;
@@ -80,13 +82,14 @@ void finish_slot(polar_server *s, Slot &sl, int status) {
   s->cv_done.notify_all();
 }
 
-void scheduler(polar_server *s) {
+void scheduler(polar_server *s, size_t first, size_t step) {
   cudaSetDevice(s->cfg.device);
   std::unique_lock<std::mutex> lk(s->mu);
   while (true) {
     bool any_busy = false;
-    // 1. completions
-    for (auto &sl : s->slots) {
+    // 1. completions of this thread's slots
+    for (size_t si = first; si < s->slots.size(); si += step) {
+      Slot &sl = s->slots[si];
       if (!sl.busy) continue;
       cudaError_t q = cudaEventQuery(sl.done);
       if (q == cudaSuccess) {
@@ -113,14 +116,14 @@ void scheduler(polar_server *s) {
         continue;
       }
       Slot *pick = nullptr;
-      for (auto &sl : s->slots)                        // a free slot that fits as is
-        if (!sl.busy && sl.ws_bytes >= need) { pick = &sl; break; }
-      if (!pick)
-        for (auto &sl : s->slots)                      // or one that may grow
-          if (!sl.busy && s->ws_total - sl.ws_bytes + need <= s->cfg.mem_budget) {
-            pick = &sl;
-            break;
-          }
+      for (size_t si = first; si < s->slots.size() && !pick; si += step) {
+        Slot &sl = s->slots[si];                       // a free slot that fits as is
+        if (!sl.busy && sl.ws_bytes >= need) pick = &sl;
+      }
+      for (size_t si = first; si < s->slots.size() && !pick; si += step) {
+        Slot &sl = s->slots[si];                       // or one that may grow
+        if (!sl.busy && s->ws_total - sl.ws_bytes + need <= s->cfg.mem_budget) pick = &sl;
+      }
       if (!pick) break;
       Pending job = p;
       s->queue.pop_front();
@@ -128,6 +131,7 @@ void scheduler(polar_server *s) {
         s->ws_total += need - pick->ws_bytes;
         pick->ws_bytes = need;
       }
+      pick->busy = true;                               // reserved while launching
       auto it = s->records.find(job.ticket);
       if (it != s->records.end()) it->second.t_launch = Clock::now();
       lk.unlock();
@@ -140,10 +144,8 @@ void scheduler(polar_server *s) {
       pick->ticket = job.ticket;
       s->launched++;
       if (rc != POLAR_OK) {
-        pick->busy = true;
         finish_slot(s, *pick, rc);
       } else {
-        pick->busy = true;
         any_busy = true;
       }
     }
@@ -168,6 +170,7 @@ int polar_server_create(const polar_server_config *cfg, polar_server **out) {
   if (cfg->fkind != POLAR_F_MINSUM && cfg->fkind != POLAR_F_EXACT) return POLAR_EINVAL;
   if (cfg->prec != POLAR_FP32 && cfg->prec != POLAR_FP16 && cfg->prec != POLAR_INT8)
     return POLAR_EINVAL;
+  if (cfg->threads < 0 || cfg->threads > 16) return POLAR_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
     cudaGetLastError();
@@ -193,7 +196,9 @@ int polar_server_create(const polar_server_config *cfg, polar_server **out) {
     }
   }
   cudaSetDevice(prev);
-  s->thread = std::thread(scheduler, s);
+  size_t nth = cfg->threads ? (size_t)cfg->threads : 4;
+  if (nth > s->slots.size()) nth = s->slots.size();
+  for (size_t i = 0; i < nth; ++i) s->threads.emplace_back(scheduler, s, i, nth);
   *out = s;
   return POLAR_OK;
 }
@@ -269,7 +274,8 @@ void polar_server_destroy(polar_server *s) {
     s->stop = true;
   }
   s->cv_done.notify_all();
-  if (s->thread.joinable()) s->thread.join();
+  for (auto &th : s->threads)
+    if (th.joinable()) th.join();
   for (auto &sl : s->slots) {
     cudaStreamSynchronize(sl.stream);
     polar::release_stream_workspace(s->cfg.device, sl.stream);

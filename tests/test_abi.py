@@ -110,9 +110,10 @@ def test_frozen_set_from_mask_roundtrip(P):
 def test_server_config_rejected_on_host(P):
     import ctypes as C
     h = C.c_void_p()
-    for cfg in (P.ServerConfig(0, 0, 16, 1 << 30, 0, 0), P.ServerConfig(0, 4, 0, 1 << 30, 0, 0),
-                P.ServerConfig(0, 4, 16, 1 << 30, 5, 0), P.ServerConfig(0, 4, 16, 1 << 30, 0, 7),
-                P.ServerConfig(-1, 4, 16, 1 << 30, 0, 0)):
+    for cfg in (P.ServerConfig(0, 0, 16, 1 << 30, 0, 0, 0), P.ServerConfig(0, 4, 0, 1 << 30, 0, 0, 0),
+                P.ServerConfig(0, 4, 16, 1 << 30, 5, 0, 0), P.ServerConfig(0, 4, 16, 1 << 30, 0, 7, 0),
+                P.ServerConfig(0, 4, 16, 1 << 30, 0, 0, 99),
+                P.ServerConfig(-1, 4, 16, 1 << 30, 0, 0, 0)):
         assert P.lib().polar_server_create(C.byref(cfg), C.byref(h)) == P.POLAR_EINVAL
     assert P.lib().polar_server_submit(None, None, None) == P.POLAR_EINVAL
     assert P.lib().polar_server_poll(None, 1, None) == P.POLAR_EINVAL
