@@ -255,7 +255,9 @@ int polar_server_create(const polar_server_config *cfg, polar_server **out);
 
 /* Queue a request; *ticket identifies it.  EINVAL: bad request (checked on
  * the host); EBUSY: the queue holds max_queue requests (admission refused,
- * retry later).  The caller keeps every buffer alive until completion. */
+ * retry later).  The caller keeps every buffer alive until completion, and
+ * its inputs must already be complete on the device when submit is called:
+ * the server's streams do not wait on any of the caller's streams. */
 int polar_server_submit(polar_server *srv, const polar_request *req, uint64_t *ticket);
 
 /* POLAR_PENDING while the request runs; once done, its final status (OK or

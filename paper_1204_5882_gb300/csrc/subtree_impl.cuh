@@ -255,12 +255,25 @@ struct Tile<5, FK, S, UH> {
   }
 };
 
-template <typename S>
+// The CTA of NW warps decoding one subtree.  Shared-memory levels use every
+// thread; register tiles and the 32-leaf decoder run in warp 0 only.
+template <typename S, int NW>
 struct Warp {
+  static constexpr uint32_t nth = 32 * NW;
   S *L;
   uint32_t *beta, *uh, *msk, *fvw;
   const uint32_t *cr0, *cr1;   // class table: bit 2^(t-k) + (o >> k) for level k >= 5
   int lane, t;
+  uint32_t tid;
+
+  __device__ __forceinline__ void sync() const {
+    if (NW == 1) __syncwarp();
+    else __syncthreads();
+  }
+  __device__ __forceinline__ bool any(bool b) const {
+    if (NW == 1) return __any_sync(FULL, b);
+    return __syncthreads_or(b) != 0;
+  }
   float sc;                    // int8 per-frame scale (1 otherwise)
   float *gbuf;                 // 32 floats: gather buffer of the register tiles
 
@@ -339,34 +352,16 @@ struct Warp {
     __syncwarp();
   }
 
-  __device__ int node_class(int k, uint32_t o) const {
-    if (k < 5) {
-      uint32_t m = low_mask(1 << k);
-      uint32_t b = (msk[o >> 5] >> (o & 31)) & m;
-      return b == m ? NODE_RATE0 : (b == 0 ? NODE_RATE1 : NODE_MIXED);
-    }
-    uint32_t nw = 1u << (k - 5), w0 = o >> 5;
-    bool all1 = true, all0 = true;
-    for (uint32_t i = lane; i < nw; i += 32) {
-      uint32_t v = msk[w0 + i];
-      all1 &= (v == FULL);
-      all0 &= (v == 0u);
-    }
-    all1 = __all_sync(FULL, all1);
-    all0 = __all_sync(FULL, all0);
-    return all1 ? NODE_RATE0 : (all0 ? NODE_RATE1 : NODE_MIXED);
-  }
-
   // Cross-word transform levels of the words [w0, w0 + nw) of `v`.
   __device__ void xword_encode(uint32_t *v, uint32_t w0, uint32_t nw) const {
     for (uint32_t hw = 1; hw < nw; hw <<= 1) {
-      __syncwarp();
-      for (uint32_t j = lane; j < nw / 2; j += 32) {
+      sync();
+      for (uint32_t j = tid; j < nw / 2; j += nth) {
         uint32_t a = (j / hw) * 2 * hw + (j % hw);
         v[w0 + a] ^= v[w0 + a + hw];
       }
     }
-    __syncwarp();
+    sync();
   }
 
   __device__ void insert(uint32_t *v, uint32_t o, int nbits, uint32_t bits) const {
@@ -378,19 +373,19 @@ struct Warp {
   __device__ void rate0(int k, uint32_t o) const {
     if (k >= 5) {
       uint32_t w0 = o >> 5, nw = 1u << (k - 5);
-      for (uint32_t i = lane; i < nw; i += 32) {
+      for (uint32_t i = tid; i < nw; i += nth) {
         uint32_t v = fvw[w0 + i];
         if (UH) uh[w0 + i] = v;
         beta[w0 + i] = encode_word(v, 5);
       }
       xword_encode(beta, w0, nw);
     } else {
-      if (lane == 0) {
+      if (tid == 0) {
         uint32_t v = (fvw[o >> 5] >> (o & 31)) & low_mask(1 << k);
         insert(uh, o, 1 << k, v);
         insert(beta, o, 1 << k, encode_word(v, k));
       }
-      __syncwarp();
+      sync();
     }
   }
 
@@ -401,7 +396,7 @@ struct Warp {
   __device__ bool rate1(int k, uint32_t o) const {
     const S *Lk = lvl(k);
     const uint32_t w0 = o >> 5, nw = 1u << (k - 5);
-    if (nw == 1) {
+    if (NW == 1 && nw == 1) {
       const float v = Store<S>::ld(Lk + lane);
       if (__any_sync(FULL, v == 0.0f)) return false;
       const uint32_t b = __ballot_sync(FULL, v < 0.0f);
@@ -416,7 +411,7 @@ struct Warp {
     uint32_t words[8];                   // nw <= 2^(t-5) <= 512: 16 words per lane at most
 #pragma unroll
     for (int r = 0; r < 8; ++r) words[r] = 0u;
-    for (uint32_t i = lane, r = 0; i < nw; i += 32, ++r) {
+    for (uint32_t i = tid, r = 0; i < nw; i += nth, ++r) {
       uint32_t b = 0u;
       const S *q = Lk + 32 * i;
       if constexpr (sizeof(S) == 4) {   // level k >= 6 starts 16-byte aligned
@@ -438,27 +433,27 @@ struct Warp {
       if (r < 8) words[r] = b;
       else beta[w0 + i] = b;             // beyond the register window: park directly
     }
-    if (__any_sync(FULL, z)) return false;
-    for (uint32_t i = lane, r = 0; i < nw && r < 8; i += 32, ++r) beta[w0 + i] = words[r];
+    if (any(z)) return false;
+    for (uint32_t i = tid, r = 0; i < nw && r < 8; i += nth, ++r) beta[w0 + i] = words[r];
     if (UH) {
-      __syncwarp();
-      for (uint32_t i = lane; i < nw; i += 32) uh[w0 + i] = encode_word(beta[w0 + i], 5);
+      sync();
+      for (uint32_t i = tid; i < nw; i += nth) uh[w0 + i] = encode_word(beta[w0 + i], 5);
       xword_encode(uh, w0, nw);
     } else {
-      __syncwarp();
+      sync();
     }
     return true;
   }
 
   __device__ void leaf(uint32_t o) const {
-    if (lane == 0) {
+    if (tid == 0) {
       uint32_t w = o >> 5, s = o & 31;
       uint32_t u = ((msk[w] >> s) & 1u) ? ((fvw[w] >> s) & 1u)
                                         : (uint32_t)(Store<S>::ld(lvl(0)) < 0.0f);
       insert(beta, o, 1, u);
       insert(uh, o, 1, u);
     }
-    __syncwarp();
+    sync();
   }
 
   template <int FK>
@@ -466,22 +461,22 @@ struct Warp {
     const S *__restrict__ a = lvl(k);
     S *__restrict__ c = lvl(k - 1);
     const uint32_t h = 1u << (k - 1);
-    if (h >= 128) {
-      for (uint32_t i = lane; i < h; i += 128) {
+    if (h >= 4 * nth) {
+      for (uint32_t i = tid; i < h; i += 4 * nth) {
         float x[4], y[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          x[q] = Store<S>::ld(a + i + 32 * q);
-          y[q] = Store<S>::ld(a + h + i + 32 * q);
+          x[q] = Store<S>::ld(a + i + nth * q);
+          y[q] = Store<S>::ld(a + h + i + nth * q);
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) Store<S>::st(c + i + 32 * q, f_scaled<FK>(x[q], y[q], sc));
+        for (int q = 0; q < 4; ++q) Store<S>::st(c + i + nth * q, f_scaled<FK>(x[q], y[q], sc));
       }
     } else {
-      for (uint32_t i = lane; i < h; i += 32)
+      for (uint32_t i = tid; i < h; i += nth)
         Store<S>::st(c + i, f_scaled<FK>(Store<S>::ld(a + i), Store<S>::ld(a + h + i), sc));
     }
-    __syncwarp();
+    sync();
   }
 
   // Right child of the node of level k whose left child starts at leaf o.
@@ -489,28 +484,28 @@ struct Warp {
     const S *__restrict__ a = lvl(k);
     S *__restrict__ c = lvl(k - 1);
     const uint32_t h = 1u << (k - 1);
-    if (h >= 128) {
-      for (uint32_t i = lane; i < h; i += 128) {
+    if (h >= 4 * nth) {
+      for (uint32_t i = tid; i < h; i += 4 * nth) {
         float x[4], y[4];
         uint32_t wd[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          x[q] = Store<S>::ld(a + i + 32 * q);
-          y[q] = Store<S>::ld(a + h + i + 32 * q);
-          wd[q] = beta[(o + i + 32 * q) >> 5];
+          x[q] = Store<S>::ld(a + i + nth * q);
+          y[q] = Store<S>::ld(a + h + i + nth * q);
+          wd[q] = beta[(o + i + nth * q) >> 5];
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-          Store<S>::st(c + i + 32 * q, g_bit(x[q], y[q], wd[q], (o + i) & 31));
+          Store<S>::st(c + i + nth * q, g_bit(x[q], y[q], wd[q], (o + i) & 31));
       }
     } else {
-      for (uint32_t i = lane; i < h; i += 32) {
+      for (uint32_t i = tid; i < h; i += nth) {
         uint32_t p = o + i;
         Store<S>::st(c + i, g_bit(Store<S>::ld(a + i), Store<S>::ld(a + h + i), beta[p >> 5],
                                   p & 31));
       }
     }
-    __syncwarp();
+    sync();
   }
 
   // Parent of level K at leaf base: left half ^= right half.
@@ -518,13 +513,13 @@ struct Warp {
     const uint32_t h = 1u << (K - 1);
     if (h >= 32) {
       uint32_t w0 = base >> 5, hw = h >> 5;
-      for (uint32_t i = lane; i < hw; i += 32) beta[w0 + i] ^= beta[w0 + hw + i];
-    } else if (lane == 0) {
+      for (uint32_t i = tid; i < hw; i += nth) beta[w0 + i] ^= beta[w0 + hw + i];
+    } else if (tid == 0) {
       uint32_t w = beta[base >> 5], s = base & 31;
       uint32_t r = (w >> (s + h)) & low_mask(h);
       beta[base >> 5] = w ^ (r << s);
     }
-    __syncwarp();
+    sync();
   }
 };
 
@@ -539,19 +534,25 @@ __host__ __device__ inline uint32_t bit_words(int t) {
 
 // Tin: storage of the level-t input (the streamed levels); inside the CTA
 // every level is float.
-template <typename Tin, int FK, bool SC, bool UH>
-__global__ void __launch_bounds__(32) k_subtree(StParams p, bool in_is_llr) {
+// NW warps: 4 with shortcuts (shared-memory levels spread over the CTA), 1
+// for the plain decoder.
+template <int NW, typename Tin, int FK, bool SC, bool UH>
+__global__ void __launch_bounds__(32 * NW) k_subtree(StParams p, bool in_is_llr) {
   using S = float;
+  constexpr uint32_t nth = 32 * NW;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int t = p.t;
   const uint32_t T = 1u << t;
   const uint32_t W = T >= 32 ? T / 32 : 1;
   const uint32_t CW = t >= 9 ? (1u << (t - 9)) : 1u;
-  const int lane = threadIdx.x;
+  const uint32_t tid = threadIdx.x;
+  const int lane = tid & 31;
+  const bool warp0 = tid < 32;
   const size_t fr = blockIdx.x;
 
-  Warp<S> w;
+  Warp<S, NW> w;
   w.lane = lane;
+  w.tid = tid;
   w.t = t;
   w.sc = p.scale ? p.scale[fr] : 1.0f;
   w.beta = reinterpret_cast<uint32_t *>(smraw);
@@ -566,14 +567,14 @@ __global__ void __launch_bounds__(32) k_subtree(StParams p, bool in_is_llr) {
 
   const uint64_t ow = p.o >> 5;
   const uint32_t *fvf = p.fv + fr * p.w_stride + ow;
-  for (uint32_t i = lane; i < W; i += 32) {
+  for (uint32_t i = tid; i < W; i += nth) {
     w.msk[i] = p.mask[ow + i];
     w.fvw[i] = fvf[i];
     w.beta[i] = 0u;
     w.uh[i] = 0u;
   }
   if (SC && p.cls)
-    for (uint32_t i = lane; i < 2 * CW; i += 32) ctab[i] = p.cls[i];
+    for (uint32_t i = tid; i < 2 * CW; i += nth) ctab[i] = p.cls[i];
   S *Lt = w.lvl(t);
   // Level-t LLRs into shared memory with 16-byte loads, eight in flight per
   // lane (one warp would otherwise wait a memory latency per element).
@@ -581,16 +582,16 @@ __global__ void __launch_bounds__(32) k_subtree(StParams p, bool in_is_llr) {
     const float *src = reinterpret_cast<const float *>(p.in) + fr * p.in_stride + p.o;
     if (T >= 4) {
       const float4 *s4 = reinterpret_cast<const float4 *>(src);
-      for (uint32_t b = 0; b < T / 4; b += 32 * 8) {
+      for (uint32_t b = 0; b < T / 4; b += nth * 8) {
         float4 q[8];
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
-          const uint32_t i = b + 32 * r + lane;
+          const uint32_t i = b + nth * r + tid;
           if (i < T / 4) q[r] = s4[i];
         }
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
-          const uint32_t i = b + 32 * r + lane;
+          const uint32_t i = b + nth * r + tid;
           if (i < T / 4) {
             Lt[4 * i] = rnd<Tin>(q[r].x * w.sc);
             Lt[4 * i + 1] = rnd<Tin>(q[r].y * w.sc);
@@ -600,7 +601,7 @@ __global__ void __launch_bounds__(32) k_subtree(StParams p, bool in_is_llr) {
         }
       }
     } else {
-      for (uint32_t i = lane; i < T; i += 32) Lt[i] = rnd<Tin>(src[i] * w.sc);
+      for (uint32_t i = tid; i < T; i += nth) Lt[i] = rnd<Tin>(src[i] * w.sc);
     }
   } else {
     // Tin-typed level t (16-byte chunks of 4, 8 or 16 values), widened to float
@@ -608,16 +609,16 @@ __global__ void __launch_bounds__(32) k_subtree(StParams p, bool in_is_llr) {
     constexpr uint32_t PER = 16 / sizeof(Tin);
     const uint32_t n16 = T / PER;                            // T >= 32 here
     const uint4 *s16 = reinterpret_cast<const uint4 *>(src);
-    for (uint32_t b = 0; b < n16; b += 32 * 8) {
+    for (uint32_t b = 0; b < n16; b += nth * 8) {
       uint4 q[8];
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
-        const uint32_t i = b + 32 * r + lane;
+        const uint32_t i = b + nth * r + tid;
         if (i < n16) q[r] = s16[i];
       }
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
-        const uint32_t i = b + 32 * r + lane;
+        const uint32_t i = b + nth * r + tid;
         if (i < n16) {
           const Tin *e = reinterpret_cast<const Tin *>(&q[r]);
 #pragma unroll
@@ -626,16 +627,19 @@ __global__ void __launch_bounds__(32) k_subtree(StParams p, bool in_is_llr) {
       }
     }
   }
-  __syncwarp();
+  w.sync();
 
   if (SC && t < 5) {
     // whole code shorter than a word: one register block with class checks
-    switch (t) {
-      case 1: w.template leafblock<1, FK, true, UH>(0); break;
-      case 2: w.template leafblock<2, FK, true, UH>(0); break;
-      case 3: w.template leafblock<3, FK, true, UH>(0); break;
-      default: w.template leafblock<4, FK, true, UH>(0); break;
+    if (warp0) {
+      switch (t) {
+        case 1: w.template leafblock<1, FK, true, UH>(0); break;
+        case 2: w.template leafblock<2, FK, true, UH>(0); break;
+        case 3: w.template leafblock<3, FK, true, UH>(0); break;
+        default: w.template leafblock<4, FK, true, UH>(0); break;
+      }
     }
+    w.sync();
   } else {
     int k = t;
     uint32_t o = 0;
@@ -643,7 +647,8 @@ __global__ void __launch_bounds__(32) k_subtree(StParams p, bool in_is_llr) {
       for (;;) {                                 // descend
         if (SC) {
           if (k <= 9) {                          // register tile (k = min(t, 9))
-            w.template tile_k<FK, UH>(k, o);
+            if (warp0) w.template tile_k<FK, UH>(k, o);
+            w.sync();
             break;
           }
           const int cls = w.cls_tab(k, o);
@@ -676,7 +681,7 @@ __global__ void __launch_bounds__(32) k_subtree(StParams p, bool in_is_llr) {
   uint32_t *xf = p.xhat + fr * p.w_stride + ow;
   uint32_t *uf = p.uhat ? p.uhat + fr * p.w_stride + ow : nullptr;
   const uint32_t keep = T >= 32 ? FULL : low_mask(T);
-  for (uint32_t i = lane; i < W; i += 32) {
+  for (uint32_t i = tid; i < W; i += nth) {
     xf[i] = w.beta[i] & keep;
     if (uf) uf[i] = w.uh[i] & keep;
   }
@@ -687,11 +692,12 @@ __global__ void __launch_bounds__(32) k_subtree(StParams p, bool in_is_llr) {
 template <typename Tin, int FK, bool SC, bool UH>
 cudaError_t launch_t(const SubtreeArgs &a, cudaStream_t s) {
   using S = float;
+  constexpr int NW = SC ? 4 : 1;
   const uint32_t T = 1u << a.t;
   const uint32_t W = T >= 32 ? T / 32 : 1;
   (void)W;
   size_t smem = bit_words(a.t) * sizeof(uint32_t) + 2 * (size_t)T * sizeof(S);
-  auto kern = k_subtree<Tin, FK, SC, UH>;
+  auto kern = k_subtree<NW, Tin, FK, SC, UH>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
@@ -699,7 +705,7 @@ cudaError_t launch_t(const SubtreeArgs &a, cudaStream_t s) {
   }
   StParams p{a.in,   a.in_stride, a.cls,      a.scale, a.mask, a.fv,
              a.xhat, a.uhat,      a.w_stride, a.o,     a.t,    a.r};
-  kern<<<a.nframes, 32, smem, s>>>(p, a.in_is_llr);
+  kern<<<a.nframes, 32 * NW, smem, s>>>(p, a.in_is_llr);
   return counted(cudaGetLastError(), 1);
 }
 

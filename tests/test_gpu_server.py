@@ -50,6 +50,7 @@ def make_requests(P, count, seed, sizes=(10, 12, 14, 16)):
         reqs.append(dict(n=n, F=F, fz=fz, fs=fs, L=L, fvb=fvb,
                          llr=torch.from_numpy(L).to(DEV),
                          fv=torch.from_numpy(fvw.view(np.int32)).to(DEV)))
+    torch.cuda.synchronize()          # the server's streams do not wait on torch's stream
     return reqs
 
 
@@ -66,9 +67,10 @@ def test_results_identical_alone_and_in_mix(P):
         alone.append(xh.cpu())
     srv = P.Server(max_inflight=16, max_queue=1024)
     outs, tickets = [], []
-    for r in reqs:                                   # all at once: they overlap
-        xh = torch.full_like(r["fv"], -1)
-        outs.append(xh)
+    for r in reqs:
+        outs.append(torch.full_like(r["fv"], -1))
+    torch.cuda.synchronize()                         # outputs initialised before any decode
+    for r, xh in zip(reqs, outs):                    # all at once: they overlap
         t = srv.submit(r["fs"], r["F"], r["llr"], r["fv"], xh)
         assert t is not None
         tickets.append(t)
@@ -92,10 +94,9 @@ def test_admission_refused_when_queue_full(P):
     reqs = make_requests(P, 30, 12, sizes=(16,))
     srv = P.Server(max_inflight=1, max_queue=2)
     accepted, refused = [], 0
-    outs = []
-    for r in reqs:
-        xh = torch.zeros_like(r["fv"])
-        outs.append(xh)
+    outs = [torch.zeros_like(r["fv"]) for r in reqs]
+    torch.cuda.synchronize()
+    for r, xh in zip(reqs, outs):
         t = srv.submit(r["fs"], r["F"], r["llr"], r["fv"], xh)
         if t is None:
             refused += 1
@@ -113,17 +114,16 @@ def test_memory_budget_serialises_and_rejects(P):
     reqs = make_requests(P, 6, 13, sizes=(18,))
     need = max((1 << 18) - (1 << 13), 0) * 4 * 2      # two frames of 2^18 in FP32
     srv = P.Server(max_inflight=8, max_queue=64, mem_budget=need)
-    outs, tickets = [], []
-    for r in reqs:
-        xh = torch.zeros_like(r["fv"])
-        outs.append(xh)
-        tickets.append(srv.submit(r["fs"], r["F"], r["llr"], r["fv"], xh))
+    outs = [torch.zeros_like(r["fv"]) for r in reqs]
+    torch.cuda.synchronize()
+    tickets = [srv.submit(r["fs"], r["F"], r["llr"], r["fv"], xh) for r, xh in zip(reqs, outs)]
     for t in tickets:
         assert srv.wait(t)[0] == P.POLAR_OK
     assert srv.stats()["scratch_bytes"] <= need
     # a request whose scratch alone exceeds the budget fails with ENOMEM
     big = make_requests(P, 1, 14, sizes=(20,))[0]
     xh = torch.zeros_like(big["fv"])
+    torch.cuda.synchronize()
     t = srv.submit(big["fs"], big["F"], big["llr"], big["fv"], xh)
     assert srv.wait(t)[0] == P.POLAR_ENOMEM
     srv.close()
@@ -134,6 +134,7 @@ def test_bounded_wait_and_bad_tickets(P):
     r = make_requests(P, 1, 15, sizes=(16,))[0]
     srv = P.Server(max_inflight=2)
     xh = torch.zeros_like(r["fv"])
+    torch.cuda.synchronize()
     t = srv.submit(r["fs"], r["F"], r["llr"], r["fv"], xh)
     try:
         st = srv.wait(t, 0.0)                        # may already be done
