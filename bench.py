@@ -63,6 +63,8 @@ def parse():
                          "float64 exact-f oracle on the 2^22 precision workloads")
     ap.add_argument("--sweep-frames", type=int, default=1000)
     ap.add_argument("--oracle-frames", type=int, default=96)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip polar_autotune (subtree size / fused steps) before timing")
     ap.add_argument("--subtree-log2", type=int, default=None,
                     help="override the subtree size t (library default 13)")
     return ap.parse_args()
@@ -240,6 +242,10 @@ def measure_n24(args, P, dev, steps=5, warmup=2):
             P.polar_llr_from_channel(w.channel, w.param, yd, llr, stream)
             P.polar_sc_decode_many(fs, F, llr, fv, xh, None, args.fkind, args.prec, stream)
 
+        tuned = None
+        if not args.no_autotune and args.subtree_log2 is None:
+            P.polar_llr_from_channel(w.channel, w.param, yd, llr, stream)
+            tuned = P.polar_autotune(fs, F, llr, fv, xh, args.fkind, args.prec, stream)
         for _ in range(warmup):
             step()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -255,6 +261,8 @@ def measure_n24(args, P, dev, steps=5, warmup=2):
         fer = float((xh != xd).any(dim=1).float().mean().item())
         out = {"workload": w.name, "value": F * N / (ms / 1e3) / 1e6, "unit": UNIT,
                "ms_per_step": ms, "steps": steps, "frames": F, "fer": fer,
+               "schedule": {"subtree_log2": tuned[0], "fused": bool(tuned[1])} if tuned
+               else "default",
                "inputs": "drawn on the device (torch Philox, seeded per frame)"}
         if args.plain_n24:
             P.polar_config_set("plain", 1)
@@ -312,6 +320,10 @@ def run_ours(args):
             P.polar_llr_from_channel(w.channel, w.param, yy, llr, stream)
             P.polar_sc_decode_many(fs, F, llr, ff, out, None, args.fkind, args.prec, stream)
 
+        tuned = None
+        if not args.no_autotune and args.subtree_log2 is None:
+            P.polar_llr_from_channel(w.channel, w.param, yd, llr, stream)
+            tuned = P.polar_autotune(fs, F, llr, fv, xh, args.fkind, args.prec, stream)
         for _ in range(args.warmup):
             step()
         stream.synchronize()
@@ -450,7 +462,8 @@ def run_ours(args):
 
     if dom == "subtree":
         ms, n, _ = prof["subtree"]
-        t = min(w.log2n, P.polar_config_get("subtree_log2"))
+        t = min(w.log2n, tuned[0] if tuned else (args.subtree_log2 or
+                                                 P.polar_config_get("subtree_log2")))
         ops = n * F * t * (1 << t)                  # f/g evaluations of the recursion
         ach = ops / (ms / 1e3) / 1e12
         alu_peak = sm_count * 128 * clock_ghz / 1e3  # T simple FP32 ops/s
@@ -479,7 +492,11 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.prec == "fp32" else "f32 compute, f16 storage",
-            "data": "synthetic", "config": config_of(w, args),
+            "data": "synthetic",
+            "config": config_of(w, args, {"subtree_log2": tuned[0] if tuned else
+                                          (args.subtree_log2 or 13),
+                                          "fused_streamed_steps": bool(tuned[1]) if tuned else True,
+                                          "schedule": "polar_autotune" if tuned else "default"}),
             "roofline": roof, "roofline_streamed": hbm_roof(["stream_f", "stream_g", "chain"]),
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": ck, "plain_sc": plain, "fer": fer,

@@ -78,6 +78,8 @@ const char *polar_last_error_string(void);
  *                   after another, no shortcuts, no graphs; 0 (default).
  *   "profile"       1 = time every kernel group with CUDA events (eager
  *                   launches, see polar_profile_read); 0 (default).
+ *   "autotune"      1 = use the schedule polar_autotune found for a batch
+ *                   shape (default); 0 = ignore tuned entries.
  *   "fuse"          1 = each streamed f/g step and the f steps continuing it
  *                   run as one fused column kernel (default); 0 = one launch
  *                   per step.
@@ -212,6 +214,28 @@ typedef struct {
  * frozen set whose buffers are equally strided are decoded as one batch. */
 int polar_sc_decode_batch(int nframes, const polar_frame_desc *frames,
                           polar_fkind fkind, polar_prec prec, void *stream);
+
+/* -------------------------------------------------------------- autotuning */
+
+/* Times the decode of this batch (contiguous as for polar_sc_decode_many)
+ * under each candidate schedule -- subtree sizes t = 12, 13, 14 (float32
+ * storage only: with FP16 / INT8 the rounded levels depend on t) with fused
+ * and unfused streamed steps -- and keeps the fastest for the batch shape
+ * (device, log2 N, nframes, fkind, prec).  While the "autotune" option is 1
+ * (default), later decodes of that shape use it.  Synchronous on `stream`;
+ * the batch's outputs are overwritten with valid decodes.  Any of best_t,
+ * best_fuse, best_ms may be NULL.  Decisions do not depend on the schedule
+ * (float32). */
+int polar_autotune(const polar_frozen_set *fs, int nframes, const float *llr_dev,
+                   const uint32_t *frozen_vals_dev, uint32_t *xhat_dev,
+                   polar_fkind fkind, polar_prec prec, void *stream, int *best_t,
+                   int *best_fuse, double *best_ms);
+
+/* Persist / restore the tuned table as JSON (one entry per line).  load:
+ * ENOTFOUND if the file is missing or holds no entry.  clear: forget all. */
+int polar_tune_save(const char *path);
+int polar_tune_load(const char *path);
+void polar_tune_clear(void);
 
 /* ---------------------------------------------------------------- serving */
 

@@ -3,6 +3,7 @@
 // replay as CUDA graphs.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <list>
 #include <tuple>
@@ -23,7 +24,26 @@ struct Config {
   std::atomic<long> profile{0};
   std::atomic<long> int8_target{8};
   std::atomic<long> fuse{1};
+  std::atomic<long> autotune{1};
 };
+
+// ---------------------------------------------------------------- autotuning
+// Best (subtree size, fused streamed steps) per batch shape, found by
+// polar_autotune; used by later decodes of that shape while "autotune" is 1.
+struct TuneKey {
+  int dev, log2n, nframes, fkind, prec;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(dev, log2n, nframes, fkind, prec) <
+           std::tie(o.dev, o.log2n, o.nframes, o.fkind, o.prec);
+  }
+};
+struct TuneVal {
+  int t;
+  int fuse;
+  double ms;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune;
 Config g_cfg;
 
 // ---------------------------------------------------------------- profiling
@@ -290,6 +310,21 @@ Opts current_opts() {
   return o;
 }
 
+// Options for one batch: the tuned (t, fuse) of its shape when autotuning is on.
+Opts opts_for(const polar_frozen_set *fs, int nframes, int fkind, int prec) {
+  Opts o = current_opts();
+  if (o.plain || g_cfg.autotune.load() == 0) return o;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return o;
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  auto it = g_tune.find(TuneKey{dev, (int)fs->log2n, nframes, fkind, prec});
+  if (it != g_tune.end()) {
+    o.subtree_log2 = it->second.t;
+    o.fuse = it->second.fuse != 0;
+  }
+  return o;
+}
+
 int decode_group(const Group &g, cudaStream_t s, const Opts &opt) {
   polar_frozen_set *fs = g.fs;
   const int n = (int)fs->log2n;
@@ -343,7 +378,7 @@ int decode_group(const Group &g, cudaStream_t s, const Opts &opt) {
   if (!use_graph) return run_ops(x, s, prof);
 
   GraphKey key{fs->id, g.nframes, g.llr, g.fv, g.xhat, g.uhat, g.fkind, g.prec, t,
-               shortcuts ? 1 : 0, s, dev, ws};
+               (shortcuts ? 1 : 0) | (opt.fuse ? 2 : 0), s, dev, ws};
   cudaGraphExec_t exec = nullptr;
   uint64_t kernels = 0;
   {
@@ -493,6 +528,8 @@ int polar_config_set(const char *key, long value) {
     g_cfg.profile = value ? 1 : 0;
   } else if (!strcmp(key, "fuse")) {
     g_cfg.fuse = value ? 1 : 0;
+  } else if (!strcmp(key, "autotune")) {
+    g_cfg.autotune = value ? 1 : 0;
   } else if (!strcmp(key, "int8_target")) {
     if (value < 1 || value > 64) return POLAR_EINVAL;
     g_cfg.int8_target = value;
@@ -511,6 +548,7 @@ int polar_config_get(const char *key, long *value) {
   else if (!strcmp(key, "profile")) *value = g_cfg.profile;
   else if (!strcmp(key, "int8_target")) *value = g_cfg.int8_target;
   else if (!strcmp(key, "fuse")) *value = g_cfg.fuse;
+  else if (!strcmp(key, "autotune")) *value = g_cfg.autotune;
   else return POLAR_ENOTFOUND;
   return POLAR_OK;
 }
@@ -640,7 +678,8 @@ int polar_sc_decode_many(const polar_frozen_set *fs, int nframes, const float *l
           uhat_dev, (int)fkind, (int)prec};
   int rc = check_group(g);
   if (rc) return rc;
-  return decode_group(g, static_cast<cudaStream_t>(stream), current_opts());
+  return decode_group(g, static_cast<cudaStream_t>(stream),
+                      opts_for(g.fs, g.nframes, g.fkind, g.prec));
 }
 
 int polar_sc_decode(const polar_frozen_set *fs, const float *llr_dev,
@@ -648,6 +687,112 @@ int polar_sc_decode(const polar_frozen_set *fs, const float *llr_dev,
                     polar_fkind fkind, polar_prec prec, void *stream) {
   return polar_sc_decode_many(fs, 1, llr_dev, frozen_vals_dev, xhat_dev, uhat_dev, fkind, prec,
                               stream);
+}
+
+int polar_autotune(const polar_frozen_set *fs_c, int nframes, const float *llr_dev,
+                   const uint32_t *frozen_vals_dev, uint32_t *xhat_dev, polar_fkind fkind,
+                   polar_prec prec, void *stream, int *best_t, int *best_fuse, double *best_ms) {
+  Group g{const_cast<polar_frozen_set *>(fs_c), nframes, llr_dev, frozen_vals_dev, xhat_dev,
+          nullptr, (int)fkind, (int)prec};
+  int rc = check_group(g);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int n = (int)g.fs->log2n;
+  // FP16 / INT8 round the levels >= t, so t changes their results: tune only
+  // the fused / unfused streamed steps there.
+  std::vector<int> ts;
+  if (prec == POLAR_FP32 && n > 12) {
+    for (int t = 12; t <= 14 && t <= n; ++t) ts.push_back(t);
+  } else {
+    ts.push_back(std::min<int>(n, (int)g_cfg.subtree_log2.load()));
+  }
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  TuneVal best{ts[0], 1, 1e30};
+  for (int t : ts) {
+    for (int fuse = 0; fuse <= 1; ++fuse) {
+      Opts o = current_opts();
+      o.plain = false;
+      o.profile = false;
+      o.subtree_log2 = t;
+      o.fuse = fuse != 0;
+      for (int rep = 0; rep < 2; ++rep) {              // warm: workspace, plan, graph
+        rc = decode_group(g, s, o);
+        if (rc) break;
+      }
+      if (rc) break;
+      CK(cudaEventRecord(e0, s));
+      for (int rep = 0; rep < 3 && !rc; ++rep) rc = decode_group(g, s, o);
+      if (rc) break;
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms / 3.0 < best.ms) best = TuneVal{t, fuse, ms / 3.0};
+    }
+    if (rc) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[TuneKey{dev, n, nframes, (int)fkind, (int)prec}] = best;
+  }
+  if (best_t) *best_t = best.t;
+  if (best_fuse) *best_fuse = best.fuse;
+  if (best_ms) *best_ms = best.ms;
+  return POLAR_OK;
+}
+
+int polar_tune_save(const char *path) {
+  if (!path) return POLAR_EINVAL;
+  FILE *f = fopen(path, "w");
+  if (!f) return POLAR_EINVAL;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  fprintf(f, "{\"polar_tune\": [\n");
+  size_t i = 0;
+  for (auto &kv : g_tune) {
+    fprintf(f,
+            "  {\"device\": %d, \"log2n\": %d, \"nframes\": %d, \"fkind\": %d, "
+            "\"prec\": %d, \"subtree_log2\": %d, \"fuse\": %d, \"ms\": %.6f}%s\n",
+            kv.first.dev, kv.first.log2n, kv.first.nframes, kv.first.fkind, kv.first.prec,
+            kv.second.t, kv.second.fuse, kv.second.ms, ++i < g_tune.size() ? "," : "");
+  }
+  fprintf(f, "]}\n");
+  fclose(f);
+  return POLAR_OK;
+}
+
+int polar_tune_load(const char *path) {
+  if (!path) return POLAR_EINVAL;
+  FILE *f = fopen(path, "r");
+  if (!f) return POLAR_ENOTFOUND;
+  char line[512];
+  int loaded = 0;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  while (fgets(line, sizeof line, f)) {
+    TuneKey k;
+    TuneVal v;
+    if (sscanf(line,
+               " {\"device\": %d, \"log2n\": %d, \"nframes\": %d, \"fkind\": %d, "
+               "\"prec\": %d, \"subtree_log2\": %d, \"fuse\": %d, \"ms\": %lf",
+               &k.dev, &k.log2n, &k.nframes, &k.fkind, &k.prec, &v.t, &v.fuse, &v.ms) == 8) {
+      if (v.t < 5 || v.t > 14) continue;
+      g_tune[k] = v;
+      ++loaded;
+    }
+  }
+  fclose(f);
+  return loaded > 0 ? POLAR_OK : POLAR_ENOTFOUND;
+}
+
+void polar_tune_clear(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.clear();
 }
 
 int polar_sc_decode_batch(int nframes, const polar_frame_desc *frames, polar_fkind fkind,
@@ -676,7 +821,8 @@ int polar_sc_decode_batch(int nframes, const polar_frame_desc *frames, polar_fki
     }
     Group g{const_cast<polar_frozen_set *>(a.fs), j - i, a.llr, a.frozen_vals, a.xhat, a.uhat,
             (int)fkind, (int)prec};
-    int rc = decode_group(g, static_cast<cudaStream_t>(stream), current_opts());
+    int rc = decode_group(g, static_cast<cudaStream_t>(stream),
+                          opts_for(g.fs, g.nframes, g.fkind, g.prec));
     if (rc) return rc;
     i = j;
   }

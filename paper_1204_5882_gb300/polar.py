@@ -83,6 +83,11 @@ def _load():
         "polar_sc_decode_many": ([P, I, P, P, P, P, I, I, P], I),
         "polar_sc_decode_batch": ([I, C.POINTER(FrameDesc), I, I, P], I),
         "polar_sc_decode_many_noalloc": ([P, I, P, P, P, P, I, I, P], I),
+        "polar_autotune": ([P, I, P, P, P, I, I, P, C.POINTER(I), C.POINTER(I),
+                            C.POINTER(D)], I),
+        "polar_tune_save": ([C.c_char_p], I),
+        "polar_tune_load": ([C.c_char_p], I),
+        "polar_tune_clear": ([], None),
         "polar_server_create": ([C.POINTER(ServerConfig), C.POINTER(P)], I),
         "polar_server_submit": ([P, C.POINTER(Request), C.POINTER(U64)], I),
         "polar_server_poll": ([P, U64, C.POINTER(Result)], I),
@@ -246,6 +251,33 @@ def polar_sc_decode_many_noalloc(fs: FrozenSet, nframes: int, llr, fval, xhat, u
     _check("polar_sc_decode_many_noalloc", _lib.polar_sc_decode_many_noalloc(
         fs.handle, int(nframes), _ptr(llr), _ptr(fval), _ptr(xhat), _ptr(uhat), FKIND[fkind],
         PREC[prec], _stream(stream)))
+
+
+# ------------------------------------------------------------------ autotuning
+def polar_autotune(fs: FrozenSet, nframes: int, llr, fval, xhat, fkind="minsum", prec="fp32",
+                   stream=None):
+    """(best_t, best_fuse, best_ms) for this batch shape; later decodes use it."""
+    t, fu, ms = C.c_int(), C.c_int(), C.c_double()
+    _check("polar_autotune", _lib.polar_autotune(
+        fs.handle, int(nframes), _ptr(llr), _ptr(fval), _ptr(xhat), FKIND[fkind], PREC[prec],
+        _stream(stream), C.byref(t), C.byref(fu), C.byref(ms)))
+    return t.value, fu.value, ms.value
+
+
+def polar_tune_save(path: str):
+    _check("polar_tune_save", _lib.polar_tune_save(path.encode()))
+
+
+def polar_tune_load(path: str) -> bool:
+    rc = _lib.polar_tune_load(path.encode())
+    if rc == POLAR_ENOTFOUND:
+        return False
+    _check("polar_tune_load", rc)
+    return True
+
+
+def polar_tune_clear():
+    _lib.polar_tune_clear()
 
 
 # ------------------------------------------------------------------ serving

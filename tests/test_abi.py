@@ -117,3 +117,22 @@ def test_server_config_rejected_on_host(P):
         assert P.lib().polar_server_create(C.byref(cfg), C.byref(h)) == P.POLAR_EINVAL
     assert P.lib().polar_server_submit(None, None, None) == P.POLAR_EINVAL
     assert P.lib().polar_server_poll(None, 1, None) == P.POLAR_EINVAL
+
+
+def test_tune_table_roundtrip(P, tmp_path):
+    src = tmp_path / "tune_in.json"
+    src.write_text(
+        '{"polar_tune": [\n'
+        '  {"device": 0, "log2n": 20, "nframes": 64, "fkind": 0, "prec": 0, '
+        '"subtree_log2": 14, "fuse": 1, "ms": 9.5},\n'
+        '  {"device": 0, "log2n": 24, "nframes": 16, "fkind": 1, "prec": 1, '
+        '"subtree_log2": 13, "fuse": 0, "ms": 100.25}\n]}\n')
+    P.polar_tune_clear()
+    assert P.polar_tune_load(str(src))
+    out = tmp_path / "tune_out.json"
+    P.polar_tune_save(str(out))
+    text = out.read_text()
+    assert '"log2n": 20, "nframes": 64' in text and '"subtree_log2": 14, "fuse": 1' in text
+    assert '"log2n": 24, "nframes": 16, "fkind": 1, "prec": 1, "subtree_log2": 13' in text
+    assert not P.polar_tune_load(str(tmp_path / "missing.json"))
+    P.polar_tune_clear()

@@ -294,3 +294,28 @@ def test_reduced_storage_workload_bitexact(P, prec):
         t = min(w.log2n, P.polar_config_get("subtree_log2"))
         ou, ox = O.sc_decode_store(L, ofz, fv, "minsum", prec, sc, min_level=t)
         assert np.array_equal(S.unpack_bits(xh[f], w.N), ox), f
+
+
+def test_autotune_picks_a_schedule_and_keeps_results(P):
+    w = S.Workload("tune", "bsc", 0.03, 16, 0.7, 8, 0x5EED + 50)
+    fs = P.polar_build_frozen_set(w.log2n, w.channel, w.param, w.rate)
+    x, y = S.frames(w, 0, w.frames)
+    xd = to_dev_words(x)
+    fv = torch.empty_like(xd)
+    P.polar_reveal(fs, w.frames, xd, fv)
+    llr = torch.empty(w.frames, w.N, dtype=torch.float32, device=DEV)
+    P.polar_llr_from_channel("bsc", w.param, to_dev_words(y), llr)
+    xh = torch.zeros_like(xd)
+    P.polar_tune_clear()
+    t, fuse, ms = P.polar_autotune(fs, w.frames, llr, fv, xh)
+    assert t in (12, 13, 14) and fuse in (0, 1) and ms > 0
+    xh2 = torch.zeros_like(xd)
+    P.polar_sc_decode_many(fs, w.frames, llr, fv, xh2)       # uses the tuned schedule
+    torch.cuda.synchronize()
+    ofz, _ = O.frozen_set(w.log2n, w.channel, w.param, w.rate)
+    got = words_np(xh2)
+    for f in range(w.frames):
+        _, ox, _ = O.decode_frame(w.channel, w.param, x[f], y[f], ofz, "minsum", 32)
+        assert np.array_equal(S.unpack_bits(got[f], w.N), ox)
+    assert torch.equal(xh, xh2)
+    P.polar_tune_clear()
