@@ -67,6 +67,8 @@ def parse():
                     help="skip polar_autotune (subtree size / fused steps) before timing")
     ap.add_argument("--subtree-log2", type=int, default=None,
                     help="override the subtree size t (library default 13)")
+    ap.add_argument("--fuse", type=int, choices=[0, 1], default=None,
+                    help="override fused (1) or per-level (0) streamed steps")
     return ap.parse_args()
 
 
@@ -495,7 +497,8 @@ def run_ours(args):
             "data": "synthetic",
             "config": config_of(w, args, {"subtree_log2": tuned[0] if tuned else
                                           (args.subtree_log2 or 13),
-                                          "fused_streamed_steps": bool(tuned[1]) if tuned else True,
+                                          "fused_streamed_steps": bool(tuned[1]) if tuned else
+                                          (args.fuse != 0),
                                           "schedule": "polar_autotune" if tuned else "default"}),
             "roofline": roof, "roofline_streamed": hbm_roof(["stream_f", "stream_g", "chain"]),
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
@@ -710,6 +713,9 @@ def main():
     if args.subtree_log2 is not None and args.impl == "ours":
         from paper_1204_5882_gb300 import polar as P
         P.polar_config_set("subtree_log2", args.subtree_log2)
+    if args.fuse is not None and args.impl == "ours":
+        from paper_1204_5882_gb300 import polar as P
+        P.polar_config_set("fuse", args.fuse)
     if args.impl == "reference":
         run_reference(args)
     elif args.serve:

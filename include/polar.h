@@ -86,6 +86,11 @@ const char *polar_last_error_string(void);
  *   "int8_target"   INT8 storage: the per-frame scale is the power of two
  *                   2^rint(log2(target / mean|L|)) (mean in double over the
  *                   frame's channel LLRs); 1..64, default 8.
+ *   "persistent"    how polar_sc_decode_batch runs float32 batches: 0 =
+ *                   always as launched groups of equally strided frames;
+ *                   1 (default) = in one persistent launch
+ *                   (polar_sc_decode_persistent) when the batch holds more
+ *                   than one such group; 2 = always persistent.
  */
 int polar_config_set(const char *key, long value);
 int polar_config_get(const char *key, long *value);
@@ -98,8 +103,8 @@ uint64_t polar_kernel_launches(void);
  * decode and map calls launch eagerly (no graphs) and bracket every kernel
  * group with CUDA events on the launching stream.  polar_profile_read
  * synchronises the recorded events and returns, for one kind ("llr",
- * "stream_f", "stream_g", "subtree", "rate0", "chain"), the summed device
- * time in ms,
+ * "stream_f", "stream_g", "subtree", "rate0", "chain", "persist"), the
+ * summed device time in ms,
  * the number of launches and the algorithmic bytes those launches move
  * (inputs read once, outputs written once).  polar_profile_reset discards
  * what was recorded.  Any pointer may be NULL. */
@@ -211,9 +216,30 @@ typedef struct {
 } polar_frame_desc;
 
 /* Frames of any lengths and frozen sets.  Consecutive frames with the same
- * frozen set whose buffers are equally strided are decoded as one batch. */
+ * frozen set whose buffers are equally strided are decoded as one batch;
+ * with float32 storage the "persistent" option may instead send the whole
+ * batch through polar_sc_decode_persistent. */
 int polar_sc_decode_batch(int nframes, const polar_frame_desc *frames,
                           polar_fkind fkind, polar_prec prec, void *stream);
+
+/* Frames of any lengths and frozen sets decoded by ONE persistent launch
+ * (Sec. 4's SC recursion, whole frames per CTA).  The frames form a device
+ * work queue, longest first; each CTA (four warps; as many per SM as shared
+ * memory allows for subtrees of 2^t leaves, t = the "subtree_log2" option)
+ * claims the next frame and decodes it completely: the levels above t
+ * stream through a per-CTA slice of the workspace, every 2^t-leaf subtree is
+ * decoded in shared memory, rate-0 nodes take beta = fv F^{(x)k}.  Frames
+ * never wait on one another, so a long frame overlaps many short ones.
+ * Results are bit-identical to polar_sc_decode_many (same float32 f and g on
+ * the same operands; min-sum x_hat / u_hat equal the float32 oracle).
+ * prec: POLAR_FP32 only (POLAR_EINVAL otherwise).  Every llr must be 16-byte
+ * aligned, frozen_vals / xhat / uhat 4-byte aligned (POLAR_EINVAL).
+ * Workspace: the per-stream workspace grows (cudaMalloc) to 256 B + 64 B per
+ * frame + CTAs * 4 * (2^nmax - 2^t) bytes (nmax = the longest frame), so the
+ * call must not be inside a stream capture; the frame table is copied from
+ * host memory with cudaMemcpyAsync before the launch returns. */
+int polar_sc_decode_persistent(int nframes, const polar_frame_desc *frames,
+                               polar_fkind fkind, polar_prec prec, void *stream);
 
 /* -------------------------------------------------------------- autotuning */
 

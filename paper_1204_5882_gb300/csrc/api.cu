@@ -25,6 +25,7 @@ struct Config {
   std::atomic<long> int8_target{8};
   std::atomic<long> fuse{1};
   std::atomic<long> autotune{1};
+  std::atomic<long> persistent{1};
 };
 
 // ---------------------------------------------------------------- autotuning
@@ -52,8 +53,9 @@ struct ProfRec {
   cudaEvent_t a, b;
   double bytes;
 };
-const char *const kKinds[] = {"llr", "stream_f", "stream_g", "subtree", "rate0", "chain"};
-constexpr int kNumKinds = 6;
+const char *const kKinds[] = {"llr",   "stream_f", "stream_g", "subtree",
+                              "rate0", "chain",    "persist"};
+constexpr int kNumKinds = 7;
 std::mutex g_prof_mu;
 std::vector<ProfRec> g_prof_pending;
 double g_prof_ms[kNumKinds];
@@ -429,6 +431,95 @@ int check_group(const Group &g) {
   return POLAR_OK;
 }
 
+int check_frames(int nframes, const polar_frame_desc *frames, int fkind, int prec) {
+  if (nframes < 1 || !frames) return POLAR_EINVAL;
+  for (int i = 0; i < nframes; ++i) {
+    Group one{const_cast<polar_frozen_set *>(frames[i].fs), 1, frames[i].llr,
+              frames[i].frozen_vals, frames[i].xhat, frames[i].uhat, fkind, prec};
+    int rc = check_group(one);
+    if (rc) return rc;
+  }
+  return POLAR_OK;
+}
+
+// Whole frames per CTA from a device queue (persist.cu).  The queue is
+// ordered longest first so that the long frames start early and the short
+// ones fill in behind them.
+int decode_persistent(int nframes, const polar_frame_desc *frames, int fkind, int prec,
+                      cudaStream_t s) {
+  if (prec != POLAR_FP32) {
+    g_last_error = "the persistent decoder keeps float32 levels";
+    return POLAR_EINVAL;
+  }
+  int dev = 0;
+  int rc = current_device(&dev);
+  if (rc) return rc;
+  const int tc = (int)g_cfg.subtree_log2.load();
+  std::vector<int> order(nframes);
+  for (int i = 0; i < nframes; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return frames[a].fs->log2n > frames[b].fs->log2n;
+  });
+  std::vector<PFrame> h(nframes);
+  int nmax = 0;
+  bool uh = false;
+  double alg = 0;
+  for (int j = 0; j < nframes; ++j) {
+    const polar_frame_desc &d = frames[order[j]];
+    polar_frozen_set *fs = const_cast<polar_frozen_set *>(d.fs);
+    const int n = (int)fs->log2n, t = std::min(n, tc);
+    cudaError_t e = cudaSuccess;
+    PFrame &p = h[j];
+    p.llr = d.llr;
+    p.fv = d.frozen_vals;
+    p.xhat = d.xhat;
+    p.uhat = d.uhat;
+    p.log2n = (uint32_t)n;
+    p.t = (uint32_t)t;
+    p.mask = device_mask(fs, dev, &e);
+    if (!p.mask) return e == cudaErrorMemoryAllocation ? POLAR_ENOMEM : cuda_fail(e);
+    p.cls = nullptr;
+    if (t >= 5) {
+      p.cls = device_class_table(fs, dev, t, &e);
+      if (!p.cls) return e == cudaErrorMemoryAllocation ? POLAR_ENOMEM : cuda_fail(e);
+    }
+    p.ucls = nullptr;
+    if (n > t) {
+      p.ucls = device_upper_class_table(fs, dev, t, &e);
+      if (!p.ucls) return e == cudaErrorMemoryAllocation ? POLAR_ENOMEM : cuda_fail(e);
+    }
+    nmax = std::max(nmax, n);
+    uh |= d.uhat != nullptr;
+    const double N = double(uint64_t(1) << n), sl = n - t;
+    alg += (3.0 * sl + 1.0) * N * 4.0 + (0.3125 * sl + 0.375) * N;
+  }
+  const int per_sm = persistent_ctas_per_sm(fkind, uh, tc);
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (per_sm < 1 || sms < 1) {
+    g_last_error = "persistent decoder: no resident CTA fits on an SM";
+    return POLAR_ECUDA;
+  }
+  const int grid = std::min(nframes, per_sm * sms);
+  uint64_t cta_floats = nmax > tc ? (uint64_t(1) << nmax) - (uint64_t(1) << tc) : 0;
+  cta_floats = (cta_floats + 63) & ~uint64_t(63);
+  const size_t tab = ((size_t)nframes * sizeof(PFrame) + 255) & ~size_t(255);
+  const size_t bytes = 256 + tab + (size_t)grid * cta_floats * sizeof(float);
+  void *ws = nullptr;
+  rc = get_workspace(dev, s, bytes, &ws);
+  if (rc) return rc;
+  uint32_t *head = static_cast<uint32_t *>(ws);
+  PFrame *ftab = reinterpret_cast<PFrame *>(static_cast<char *>(ws) + 256);
+  float *scratch = reinterpret_cast<float *>(static_cast<char *>(ws) + 256 + tab);
+  CK(cudaMemsetAsync(head, 0, sizeof(uint32_t), s));
+  CK(cudaMemcpyAsync(ftab, h.data(), (size_t)nframes * sizeof(PFrame), cudaMemcpyHostToDevice,
+                     s));
+  ProfScope ps(g_cfg.profile.load() != 0, 6, alg, s);
+  CK(launch_persistent(fkind, uh, ftab, (uint32_t)nframes, head, scratch, cta_floats, tc, grid,
+                       s));
+  return POLAR_OK;
+}
+
 }  // namespace
 
 namespace polar {
@@ -533,6 +624,9 @@ int polar_config_set(const char *key, long value) {
   } else if (!strcmp(key, "int8_target")) {
     if (value < 1 || value > 64) return POLAR_EINVAL;
     g_cfg.int8_target = value;
+  } else if (!strcmp(key, "persistent")) {
+    if (value < 0 || value > 2) return POLAR_EINVAL;
+    g_cfg.persistent = value;
   } else {
     return POLAR_ENOTFOUND;
   }
@@ -549,6 +643,7 @@ int polar_config_get(const char *key, long *value) {
   else if (!strcmp(key, "int8_target")) *value = g_cfg.int8_target;
   else if (!strcmp(key, "fuse")) *value = g_cfg.fuse;
   else if (!strcmp(key, "autotune")) *value = g_cfg.autotune;
+  else if (!strcmp(key, "persistent")) *value = g_cfg.persistent;
   else return POLAR_ENOTFOUND;
   return POLAR_OK;
 }
@@ -615,6 +710,8 @@ void polar_frozen_set_free(polar_frozen_set *fs) {
     }
   }
   for (auto &kv : fs->dmask) cudaFree(kv.second);
+  for (auto &kv : fs->dclass) cudaFree(kv.second);
+  for (auto &kv : fs->ducls) cudaFree(kv.second);
   delete fs;
 }
 
@@ -795,30 +892,46 @@ void polar_tune_clear(void) {
   g_tune.clear();
 }
 
+// Frames [i, j) that decode_batch runs as one group: same frozen set and
+// equally strided buffers.
+static int group_end(int nframes, const polar_frame_desc *frames, int i) {
+  const polar_frame_desc &a = frames[i];
+  const uint64_t N = a.fs->N;
+  const size_t W = a.fs->mask.size();
+  int j = i + 1;
+  while (j < nframes) {
+    const polar_frame_desc &b = frames[j];
+    const size_t d = (size_t)(j - i);
+    if (b.fs != a.fs || b.llr != a.llr + d * N || b.frozen_vals != a.frozen_vals + d * W ||
+        b.xhat != a.xhat + d * W || (a.uhat == nullptr) != (b.uhat == nullptr) ||
+        (a.uhat && b.uhat != a.uhat + d * W))
+      break;
+    ++j;
+  }
+  return j;
+}
+
+int polar_sc_decode_persistent(int nframes, const polar_frame_desc *frames, polar_fkind fkind,
+                               polar_prec prec, void *stream) {
+  int rc = check_frames(nframes, frames, (int)fkind, (int)prec);
+  if (rc) return rc;
+  return decode_persistent(nframes, frames, (int)fkind, (int)prec,
+                           static_cast<cudaStream_t>(stream));
+}
+
 int polar_sc_decode_batch(int nframes, const polar_frame_desc *frames, polar_fkind fkind,
                           polar_prec prec, void *stream) {
-  if (nframes < 1 || !frames) return POLAR_EINVAL;
-  for (int i = 0; i < nframes; ++i) {
-    Group one{const_cast<polar_frozen_set *>(frames[i].fs), 1, frames[i].llr,
-              frames[i].frozen_vals, frames[i].xhat, frames[i].uhat, (int)fkind, (int)prec};
-    int rc = check_group(one);
-    if (rc) return rc;
-  }
+  int rc = check_frames(nframes, frames, (int)fkind, (int)prec);
+  if (rc) return rc;
+  const long pm = g_cfg.persistent.load();
+  if (prec == POLAR_FP32 && !g_cfg.plain.load() &&
+      (pm == 2 || (pm == 1 && group_end(nframes, frames, 0) < nframes)))
+    return decode_persistent(nframes, frames, (int)fkind, (int)prec,
+                             static_cast<cudaStream_t>(stream));
   int i = 0;
   while (i < nframes) {
     const polar_frame_desc &a = frames[i];
-    const uint64_t N = a.fs->N;
-    const size_t W = a.fs->mask.size();
-    int j = i + 1;
-    while (j < nframes) {
-      const polar_frame_desc &b = frames[j];
-      const size_t d = (size_t)(j - i);
-      if (b.fs != a.fs || b.llr != a.llr + d * N || b.frozen_vals != a.frozen_vals + d * W ||
-          b.xhat != a.xhat + d * W || (a.uhat == nullptr) != (b.uhat == nullptr) ||
-          (a.uhat && b.uhat != a.uhat + d * W))
-        break;
-      ++j;
-    }
+    const int j = group_end(nframes, frames, i);
     Group g{const_cast<polar_frozen_set *>(a.fs), j - i, a.llr, a.frozen_vals, a.xhat, a.uhat,
             (int)fkind, (int)prec};
     int rc = decode_group(g, static_cast<cudaStream_t>(stream),

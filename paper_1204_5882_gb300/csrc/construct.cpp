@@ -376,4 +376,55 @@ const uint32_t *device_class_table(polar_frozen_set *fs, int device, int t, cuda
   return d;
 }
 
+// Upper levels from the subtree roots up: a node is rate 0 (rate 1) when
+// both children are.
+static std::vector<uint32_t> build_upper_class_table(const polar_frozen_set *fs, int t) {
+  const int n = (int)fs->log2n;
+  const uint32_t UW = upper_class_words(n, t);
+  std::vector<uint32_t> tab(2 * (size_t)UW, 0u);
+  std::vector<uint8_t> cur(size_t(1) << (n - t)), nxt;
+  for (uint64_t q = 0; q < cur.size(); ++q) cur[q] = node_class_host(fs, t, q << t);
+  for (int k = t;; ++k) {
+    for (uint64_t q = 0; q < cur.size(); ++q) {
+      const uint64_t i = (uint64_t(1) << (n - k)) + q;
+      if (cur[q] == NODE_RATE0) tab[i >> 5] |= 1u << (i & 31);
+      if (cur[q] == NODE_RATE1) tab[UW + (i >> 5)] |= 1u << (i & 31);
+    }
+    if (k == n) break;
+    nxt.assign(cur.size() / 2, NODE_MIXED);
+    for (uint64_t q = 0; q < nxt.size(); ++q)
+      if (cur[2 * q] == cur[2 * q + 1]) nxt[q] = cur[2 * q];
+    cur.swap(nxt);
+  }
+  return tab;
+}
+
+const uint32_t *device_upper_class_table(polar_frozen_set *fs, int device, int t,
+                                         cudaError_t *err) {
+  *err = cudaSuccess;
+  if ((int)fs->log2n <= t) return nullptr;
+  {
+    std::lock_guard<std::mutex> g(fs->mu);
+    auto it = fs->ducls.find({device, t});
+    if (it != fs->ducls.end()) return it->second;
+  }
+  const std::vector<uint32_t> tab = build_upper_class_table(fs, t);
+  uint32_t *d = nullptr;
+  *err = cudaMalloc(&d, tab.size() * sizeof(uint32_t));
+  if (*err != cudaSuccess) return nullptr;
+  *err = cudaMemcpy(d, tab.data(), tab.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+  if (*err != cudaSuccess) {
+    cudaFree(d);
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> g(fs->mu);
+  auto it = fs->ducls.find({device, t});
+  if (it != fs->ducls.end()) {
+    cudaFree(d);
+    return it->second;
+  }
+  fs->ducls[{device, t}] = d;
+  return d;
+}
+
 }  // namespace polar

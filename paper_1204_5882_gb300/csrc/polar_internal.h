@@ -14,6 +14,13 @@
 
 #include "polar.h"
 
+// Small index helpers used by host and device code.
+#ifdef __CUDACC__
+#define POLAR_HD __host__ __device__
+#else
+#define POLAR_HD
+#endif
+
 namespace polar {
 
 // Node classes of the SC tree, read from the frozen mask (Sec. 3 / Sec. 4):
@@ -57,6 +64,7 @@ struct polar_frozen_set {
   std::mutex mu;
   std::map<int, uint32_t *> dmask;                        // device -> mask copy
   std::map<std::pair<int, int>, uint32_t *> dclass;       // (device, t) -> class table
+  std::map<std::pair<int, int>, uint32_t *> ducls;        // (device, t) -> upper class table
   std::map<int, std::shared_ptr<std::vector<uint32_t>>> hclass;   // t -> host class table
   std::map<std::pair<int, int>, std::shared_ptr<polar::Plan>> plans;  // (t, flags)
 };
@@ -73,9 +81,17 @@ const uint32_t *device_mask(polar_frozen_set *fs, int device, cudaError_t *err);
 // Node-class table of every subtree of 2^t leaves (levels 5..t): per subtree
 // class_words(t) words of "rate 0" bits then as many of "rate 1" bits; node
 // (k, q) of a subtree is bit 2^(t-k) + q.
-inline uint32_t class_words(int t) { return t >= 9 ? (1u << (t - 9)) : 1u; }
+POLAR_HD inline uint32_t class_words(int t) { return t >= 9 ? (1u << (t - 9)) : 1u; }
 std::shared_ptr<std::vector<uint32_t>> class_table_host(polar_frozen_set *fs, int t);
 const uint32_t *device_class_table(polar_frozen_set *fs, int device, int t, cudaError_t *err);
+// Node-class table of the levels t..n of the whole code (n > t): node (k, q)
+// is bit 2^(n-k) + q of upper_class_words(n, t) "rate 0" words, followed by
+// as many "rate 1" words.
+POLAR_HD inline uint32_t upper_class_words(int n, int t) {
+  return n - t + 1 >= 5 ? (1u << (n - t + 1 - 5)) : 1u;
+}
+const uint32_t *device_upper_class_table(polar_frozen_set *fs, int device, int t,
+                                         cudaError_t *err);
 
 // --- kernels (stream_kernels.cu, subtree.cu) --------------------------------
 cudaError_t launch_llr_bsc(const uint32_t *y, float *llr, size_t n_total, float c,
@@ -136,6 +152,33 @@ struct SubtreeArgs {
 cudaError_t launch_subtree(const SubtreeArgs &a, cudaStream_t s);
 
 size_t storage_bytes(int prec);
+
+// --- persistent decoder (persist.cu) ------------------------------------------
+// One frame of a persistent launch.  Levels t..n-1 of the frame being decoded
+// live in the scratch of the CTA that claimed it.
+struct PFrame {
+  const float *llr;        // [2^log2n] channel LLRs, 16-byte aligned
+  const uint32_t *fv;      // frozen values, packed
+  uint32_t *xhat;          // x_hat, packed
+  uint32_t *uhat;          // u_hat, packed, or null
+  const uint32_t *mask;    // frozen mask of the code (device)
+  const uint32_t *cls;     // subtree class tables (levels 5..t, t >= 5) or null
+  const uint32_t *ucls;    // class table of the levels t..n (n > t) or null
+  uint32_t log2n;
+  uint32_t t;              // subtree size of this frame: min(log2n, the launch's t)
+};
+// Threads of a persistent CTA.
+constexpr int kPersistThreads = 128;
+// Dynamic shared memory of a persistent CTA for subtrees of up to 2^t leaves.
+size_t persistent_smem_bytes(int t);
+// Resident CTAs per SM of the persistent kernel (0 on error).
+int persistent_ctas_per_sm(int fkind, bool uhat, int t);
+// Frames [0, count) of `frames` (device) are claimed in order through *head
+// (device, zero on entry) by `grid` CTAs; CTA c keeps its levels at
+// scratch + c * cta_floats.
+cudaError_t launch_persistent(int fkind, bool uhat, const PFrame *frames, uint32_t count,
+                              uint32_t *head, float *scratch, uint64_t cta_floats, int t,
+                              int grid, cudaStream_t s);
 
 // api.cu: decoding with caller-provided device mask and level scratch.
 size_t level_scratch_bytes(const polar_frozen_set *fs, int nframes, int prec, int *t_out);

@@ -34,6 +34,7 @@ constexpr uint32_t FULL = 0xFFFFFFFFu;
 struct StParams {
   const void *in;
   size_t in_stride;
+  uint64_t in_o;         // float input: element offset of the subtree in its row
   const uint32_t *cls;   // class table of this subtree (levels 5..t), or null
   const float *scale;    // per-frame int8 scale, or null
   const uint32_t *mask;
@@ -536,11 +537,14 @@ __host__ __device__ inline uint32_t bit_words(int t) {
 // every level is float.
 // NW warps: 4 with shortcuts (shared-memory levels spread over the CTA), 1
 // for the plain decoder.
+// Decodes the subtree of frame `fr` (row fr of every strided argument) with
+// the CTA's threads; smraw is the dynamic shared memory (bit_words(t) words
+// then 2^(t+1) floats).  The whole CTA must call it.
 template <int NW, typename Tin, int FK, bool SC, bool UH>
-__global__ void __launch_bounds__(32 * NW) k_subtree(StParams p, bool in_is_llr) {
+__device__ __forceinline__ void subtree_body(const StParams &p, bool in_is_llr, size_t fr,
+                                             unsigned char *smraw) {
   using S = float;
   constexpr uint32_t nth = 32 * NW;
-  extern __shared__ __align__(16) unsigned char smraw[];
   const int t = p.t;
   const uint32_t T = 1u << t;
   const uint32_t W = T >= 32 ? T / 32 : 1;
@@ -548,7 +552,6 @@ __global__ void __launch_bounds__(32 * NW) k_subtree(StParams p, bool in_is_llr)
   const uint32_t tid = threadIdx.x;
   const int lane = tid & 31;
   const bool warp0 = tid < 32;
-  const size_t fr = blockIdx.x;
 
   Warp<S, NW> w;
   w.lane = lane;
@@ -579,7 +582,7 @@ __global__ void __launch_bounds__(32 * NW) k_subtree(StParams p, bool in_is_llr)
   // Level-t LLRs into shared memory with 16-byte loads, eight in flight per
   // lane (one warp would otherwise wait a memory latency per element).
   if (in_is_llr) {
-    const float *src = reinterpret_cast<const float *>(p.in) + fr * p.in_stride + p.o;
+    const float *src = reinterpret_cast<const float *>(p.in) + fr * p.in_stride + p.in_o;
     if (T >= 4) {
       const float4 *s4 = reinterpret_cast<const float4 *>(src);
       for (uint32_t b = 0; b < T / 4; b += nth * 8) {
@@ -689,6 +692,12 @@ __global__ void __launch_bounds__(32 * NW) k_subtree(StParams p, bool in_is_llr)
   if (p.r > 0) cascade_device(p.xhat + fr * p.w_stride, t, p.o, p.r);
 }
 
+template <int NW, typename Tin, int FK, bool SC, bool UH>
+__global__ void __launch_bounds__(32 * NW) k_subtree(StParams p, bool in_is_llr) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  subtree_body<NW, Tin, FK, SC, UH>(p, in_is_llr, blockIdx.x, smraw);
+}
+
 template <typename Tin, int FK, bool SC, bool UH>
 cudaError_t launch_t(const SubtreeArgs &a, cudaStream_t s) {
   using S = float;
@@ -703,7 +712,7 @@ cudaError_t launch_t(const SubtreeArgs &a, cudaStream_t s) {
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
-  StParams p{a.in,   a.in_stride, a.cls,      a.scale, a.mask, a.fv,
+  StParams p{a.in,   a.in_stride, a.in_is_llr ? a.o : 0, a.cls, a.scale, a.mask, a.fv,
              a.xhat, a.uhat,      a.w_stride, a.o,     a.t,    a.r};
   kern<<<a.nframes, 32 * NW, smem, s>>>(p, a.in_is_llr);
   return counted(cudaGetLastError(), 1);

@@ -82,6 +82,7 @@ def _load():
         "polar_sc_decode": ([P, P, P, P, P, I, I, P], I),
         "polar_sc_decode_many": ([P, I, P, P, P, P, I, I, P], I),
         "polar_sc_decode_batch": ([I, C.POINTER(FrameDesc), I, I, P], I),
+        "polar_sc_decode_persistent": ([I, C.POINTER(FrameDesc), I, I, P], I),
         "polar_sc_decode_many_noalloc": ([P, I, P, P, P, P, I, I, P], I),
         "polar_autotune": ([P, I, P, P, P, I, I, P, C.POINTER(I), C.POINTER(I),
                             C.POINTER(D)], I),
@@ -159,7 +160,7 @@ def polar_profile_reset():
     _lib.polar_profile_reset()
 
 
-PROFILE_KINDS = ("llr", "stream_f", "stream_g", "subtree", "rate0", "chain")
+PROFILE_KINDS = ("llr", "stream_f", "stream_g", "subtree", "rate0", "chain", "persist")
 
 
 # ------------------------------------------------------------------ frozen sets
@@ -236,14 +237,25 @@ def polar_sc_decode_many(fs: FrozenSet, nframes: int, llr, fval, xhat, uhat=None
         PREC[prec], _stream(stream)))
 
 
-def polar_sc_decode_batch(frames, fkind="minsum", prec="fp32", stream=None):
-    """frames: list of (FrozenSet, llr, fval, xhat, uhat_or_None) tensors."""
+def _frame_descs(frames):
     arr = (FrameDesc * len(frames))()
     for i, (fs, llr, fv, xh, uh) in enumerate(frames):
         arr[i] = FrameDesc(fs.handle.value, llr.data_ptr(), fv.data_ptr(), xh.data_ptr(),
                            uh.data_ptr() if uh is not None else None)
+    return arr
+
+
+def polar_sc_decode_batch(frames, fkind="minsum", prec="fp32", stream=None):
+    """frames: list of (FrozenSet, llr, fval, xhat, uhat_or_None) tensors."""
     _check("polar_sc_decode_batch", _lib.polar_sc_decode_batch(
-        len(frames), arr, FKIND[fkind], PREC[prec], _stream(stream)))
+        len(frames), _frame_descs(frames), FKIND[fkind], PREC[prec], _stream(stream)))
+
+
+def polar_sc_decode_persistent(frames, fkind="minsum", prec="fp32", stream=None):
+    """One persistent launch over frames of any lengths and codes; frames as
+    for polar_sc_decode_batch."""
+    _check("polar_sc_decode_persistent", _lib.polar_sc_decode_persistent(
+        len(frames), _frame_descs(frames), FKIND[fkind], PREC[prec], _stream(stream)))
 
 
 def polar_sc_decode_many_noalloc(fs: FrozenSet, nframes: int, llr, fval, xhat, uhat=None,

@@ -56,6 +56,9 @@ def test_strerror_and_config(P):
         P.polar_config_set("subtree_log2", 40)
     with pytest.raises(P.PolarError):
         P.polar_config_set("no_such_key", 1)
+    assert P.polar_config_get("persistent") == 1
+    with pytest.raises(P.PolarError):
+        P.polar_config_set("persistent", 3)
 
 
 def test_argument_errors_are_host_side(P):
@@ -75,6 +78,14 @@ def test_argument_errors_are_host_side(P):
     assert L.polar_llr_from_channel(1, 1.0, 16, 0, 16, 0, None) == P.POLAR_OK   # empty
     assert L.polar_encode(0, 1, 16, 16, None) == P.POLAR_EINVAL
     assert L.polar_encode(27, 1, 16, 16, None) == P.POLAR_EINVAL
+    # persistent decoder: empty queue, null table, non-float32 storage
+    desc = (P.FrameDesc * 1)(P.FrameDesc(fs.handle.value, 16, 16, 16, None))
+    assert L.polar_sc_decode_persistent(0, desc, 0, 0, None) == P.POLAR_EINVAL
+    assert L.polar_sc_decode_persistent(1, None, 0, 0, None) == P.POLAR_EINVAL
+    assert L.polar_sc_decode_persistent(1, desc, 0, 1, None) == P.POLAR_EINVAL
+    assert L.polar_sc_decode_persistent(1, desc, 0, 2, None) == P.POLAR_EINVAL
+    bad = (P.FrameDesc * 1)(P.FrameDesc(fs.handle.value, 20, 16, 16, None))   # llr not 16-B
+    assert L.polar_sc_decode_persistent(1, bad, 0, 0, None) == P.POLAR_EINVAL
     with pytest.raises(P.PolarError):
         P.polar_build_frozen_set(10, "bsc", 0.7, 0.5)
     with pytest.raises(P.PolarError):
