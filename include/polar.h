@@ -267,22 +267,37 @@ void polar_tune_clear(void);
 
 /* Continuous-batching request server (the serving pattern around the SC
  * decoder of Sec. 4; the paper itself decodes one frame at a time).
- * Requests enter a bounded host queue; a scheduler thread launches the oldest
- * pending request on a free decode slot (a non-blocking CUDA stream with its
- * own scratch) as soon as a slot is free and the scratch budget allows, so
- * requests that arrive while others run overlap with them on the device.
- * The server never touches request buffers after reporting completion. */
+ * Requests enter a bounded host queue and are admitted oldest first.  Two
+ * modes:
+ *  - slots (persistent = 0): a scheduler thread launches the oldest pending
+ *    request on a free decode slot (a non-blocking CUDA stream with its own
+ *    scratch) as soon as a slot is free and the scratch budget allows;
+ *  - persistent (persistent = 1, float32 only): one resident launch of the
+ *    persistent decoder (see polar_sc_decode_persistent) whose CTAs claim
+ *    frames from a ring in host-mapped memory; the scheduler publishes each
+ *    admitted request's frames into the ring while the launch runs and reads
+ *    per-frame completion words back, so no launch is made per request.
+ *    CTAs that find nothing to do for about a millisecond leave; the
+ *    scheduler relaunches when frames arrive.  Each CTA holds the scratch of
+ *    the longest accepted code, 4 * 2^max_log2n bytes.
+ * Either way requests that arrive while others run overlap with them on the
+ * device.  The server never touches request buffers after reporting
+ * completion. */
 typedef struct polar_server polar_server;
 
 typedef struct {
     int device;         /* CUDA device ordinal the server decodes on */
-    int max_inflight;   /* decode slots (CUDA streams), 1..256 */
+    int max_inflight;   /* slots: decode streams, 1..256; persistent: cap on
+                           resident CTAs (frames decoded at once), 1..4096 */
     int max_queue;      /* pending requests held before submit returns EBUSY */
-    size_t mem_budget;  /* bytes of decode scratch all slots may hold together */
+    size_t mem_budget;  /* bytes of decode scratch the server may hold */
     polar_fkind fkind;
     polar_prec prec;
-    int threads;        /* host scheduler threads launching work, 0 = 4; each owns
-                           an equal share of the slots (launch cost is on the host) */
+    int threads;        /* slots: host scheduler threads launching work, 0 = 4;
+                           each owns an equal share of the slots */
+    int persistent;     /* 1 = persistent mode (prec must be POLAR_FP32) */
+    int max_log2n;      /* persistent: longest code accepted, 1..26, 0 = 22;
+                           longer requests are refused at submit (EINVAL) */
 } polar_server_config;
 
 typedef struct {
@@ -304,8 +319,11 @@ typedef struct {
 int polar_server_create(const polar_server_config *cfg, polar_server **out);
 
 /* Queue a request; *ticket identifies it.  EINVAL: bad request (checked on
- * the host); EBUSY: the queue holds max_queue requests (admission refused,
- * retry later).  The caller keeps every buffer alive until completion, and
+ * the host; persistent mode also refuses codes longer than max_log2n and
+ * requests of more frames than half the ring, which holds
+ * max(1024, 4 * resident CTAs) frames rounded up to a power of two);
+ * EBUSY: the queue holds max_queue requests (admission refused, retry
+ * later).  The caller keeps every buffer alive until completion, and
  * its inputs must already be complete on the device when submit is called:
  * the server's streams do not wait on any of the caller's streams. */
 int polar_server_submit(polar_server *srv, const polar_request *req, uint64_t *ticket);
@@ -320,8 +338,9 @@ int polar_server_poll(polar_server *srv, uint64_t ticket, polar_result *out);
 int polar_server_wait(polar_server *srv, uint64_t ticket, double timeout_ms,
                       polar_result *out);
 
-/* Counters since creation: requests launched, completed, refused with EBUSY,
- * and the scratch bytes the slots hold.  Any pointer may be NULL. */
+/* Counters since creation: requests launched (slots) or published to the
+ * ring (persistent), completed, refused with EBUSY, and the scratch bytes
+ * the server holds.  Any pointer may be NULL. */
 int polar_server_stats(polar_server *srv, uint64_t *launched, uint64_t *completed,
                        uint64_t *refused, size_t *scratch_bytes);
 

@@ -226,6 +226,81 @@ __global__ void __launch_bounds__(PT) k_persist(const PFrame *frames, uint32_t c
   }
 }
 
+// ---------------------------------------------------------------- serving
+// The same frame decoder fed by a ring that the host keeps filling while the
+// launch runs (host-mapped memory): thread 0 of a CTA claims frame `head`
+// once the host has published it (tail > head), decodes it with the CTA and
+// then publishes done[i % R] = i + 1.  A CTA that finds no frame for idle_ns
+// nanoseconds, or sees `stop`, leaves; the host relaunches when frames are
+// published after the launch ended.
+__device__ __forceinline__ uint32_t ld_acquire_sys(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_sys(uint32_t *p, uint32_t v) {
+  asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+constexpr uint32_t kNoFrame = 0xFFFFFFFFu;
+
+// Thread 0: the next published frame, or kNoFrame (idle, stop, or the
+// iteration cap, which bounds the wait independently of the timer).
+__device__ uint32_t claim_frame(const ServeArgs &a) {
+  const uint64_t t0 = global_ns();
+  uint32_t nap = 128;
+  for (uint32_t it = 0; it < (1u << 22); ++it) {
+    const uint32_t tl = ld_acquire_sys(a.tail);
+    uint32_t h = *reinterpret_cast<volatile uint32_t *>(a.head);
+    while (h < tl) {                              // each failed CAS means h grew
+      const uint32_t prev = atomicCAS(a.head, h, h + 1);
+      if (prev == h) return h;
+      h = prev;
+    }
+    if (ld_acquire_sys(a.stop)) return kNoFrame;
+    if (global_ns() - t0 > a.idle_ns) return kNoFrame;
+    __nanosleep(nap);
+    nap = nap < 8192 ? 2 * nap : nap;
+  }
+  return kNoFrame;
+}
+
+template <int FK>
+__global__ void __launch_bounds__(PT) k_serve(ServeArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ uint32_t s_idx;
+  __shared__ __align__(16) PFrame s_fr;
+  float *lv = a.scratch + (uint64_t)blockIdx.x * a.cta_floats;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const uint32_t idx = claim_frame(a);
+      if (idx != kNoFrame) {                      // the ring entry, read past any cache
+        const volatile uint64_t *src =
+            reinterpret_cast<const volatile uint64_t *>(a.ring + (idx & a.rmask));
+        uint64_t *dst = reinterpret_cast<uint64_t *>(&s_fr);
+        for (int w = 0; w < (int)(sizeof(PFrame) / 8); ++w) dst[w] = src[w];
+      }
+      s_idx = idx;
+    }
+    __syncthreads();
+    const uint32_t idx = s_idx;
+    const PFrame fr = s_fr;
+    __syncthreads();
+    if (idx == kNoFrame) break;
+    decode_frame<FK, true>(fr, lv, smraw, a.S);
+    __syncthreads();                              // every x_hat / u_hat word written
+    if (threadIdx.x == 0) {
+      __threadfence_system();
+      st_release_sys(a.done + (idx & a.rmask), idx + 1);
+    }
+  }
+}
+
 template <int FK, bool UH>
 cudaError_t launch_pk(const PFrame *frames, uint32_t count, uint32_t *head, float *scratch,
                       uint64_t cta_floats, int t, int grid, cudaStream_t s) {
@@ -256,7 +331,40 @@ int occupancy(int t) {
   return nb;
 }
 
+template <int FK>
+int serve_occupancy(int t) {
+  const size_t smem = persistent_smem_bytes(t);
+  auto kern = k_serve<FK>;
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess)
+    return 0;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, PT, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nb;
+}
+
 }  // namespace
+
+int serve_ctas_per_sm(int fkind, int t) {
+  return fkind == 0 ? serve_occupancy<0>(t) : serve_occupancy<1>(t);
+}
+
+cudaError_t launch_serve(int fkind, ServeArgs a, int t, int grid, cudaStream_t s) {
+  const size_t smem = persistent_smem_bytes(t);
+  a.S = upper_stages(smem);
+  auto kern = fkind == 0 ? k_serve<0> : k_serve<1>;
+  if (smem > 48 * 1024) {
+    cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<grid, PT, smem, s>>>(a);
+  return counted(cudaGetLastError(), 1);
+}
 
 // The subtree's levels and bit vectors, and at least one stage of upper-step
 // slots (48 bytes per thread).

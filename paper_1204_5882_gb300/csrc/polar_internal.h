@@ -180,6 +180,23 @@ cudaError_t launch_persistent(int fkind, bool uhat, const PFrame *frames, uint32
                               uint32_t *head, float *scratch, uint64_t cta_floats, int t,
                               int grid, cudaStream_t s);
 
+// Serving launch: frames come from a ring in host-mapped memory that the
+// host fills while the launch runs (see persist.cu).
+struct ServeArgs {
+  const PFrame *ring;      // host-mapped, rmask + 1 entries (a power of two)
+  uint32_t rmask;
+  const uint32_t *tail;    // host-mapped: frames published so far
+  const uint32_t *stop;    // host-mapped: 1 = leave once nothing is published
+  uint32_t *done;          // host-mapped: done[i & rmask] = i + 1 once frame i is decoded
+  uint32_t *head;          // device: frames claimed so far (kept across launches)
+  float *scratch;          // grid * cta_floats floats
+  uint64_t cta_floats;
+  uint64_t idle_ns;        // a CTA leaves after this long without a frame
+  int S;                   // set by launch_serve
+};
+int serve_ctas_per_sm(int fkind, int t);
+cudaError_t launch_serve(int fkind, ServeArgs a, int t, int grid, cudaStream_t s);
+
 // api.cu: decoding with caller-provided device mask and level scratch.
 size_t level_scratch_bytes(const polar_frozen_set *fs, int nframes, int prec, int *t_out);
 int decode_with_scratch(const polar_frozen_set *fs, int nframes, const float *llr,

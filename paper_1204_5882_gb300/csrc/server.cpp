@@ -12,8 +12,19 @@
 // their work overlaps on the device.  Admission is by device memory: a slot
 // may only grow its workspace while the sum over slots stays within the
 // budget (the decode scratch of a frame is about N * bytes(storage)).
+//
+// Persistent mode keeps one launch of the persistent decoder resident
+// instead: the scheduler writes each admitted frame's descriptor into a ring
+// in host-mapped memory and publishes it by advancing `tail`; the launch's
+// CTAs claim frames in publication order and write one completion word per
+// frame back into host-mapped memory.  The scheduler turns those words into
+// request completions, recycles ring entries, and relaunches the decoder when
+// frames are waiting and the previous launch has ended (its CTAs leave after
+// about a millisecond without work).
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstring>
 #include <deque>
 #include <thread>
 #include <unordered_map>
@@ -49,8 +60,32 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
 
 }  // namespace
 
+// Persistent-mode state.
+struct Ring {
+  int t = 13;                   // subtree size of the resident launch
+  int grid = 0;                 // resident CTAs
+  uint32_t R = 0;               // ring entries (power of two)
+  polar::PFrame *ring = nullptr;          // host-mapped
+  uint32_t *ctl = nullptr;                // host-mapped: [0] tail, [1] stop, [64..) done
+  uint32_t *done = nullptr;
+  uint32_t *head = nullptr;               // device
+  float *scratch = nullptr;               // device
+  uint64_t cta_floats = 0;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  bool running = false;
+  bool stopping = false;                  // stop word set for the running launch
+  Clock::time_point last_busy;            // last time frames were outstanding
+  uint32_t published = 0;                 // frames published (tail)
+  std::deque<uint32_t> out;               // published frame indices, oldest first
+  std::vector<uint8_t> seen;              // per entry: completion observed
+  std::vector<uint64_t> ticket;           // per entry: request ticket
+  std::unordered_map<uint64_t, int> left; // ticket -> frames not yet complete
+};
+
 struct polar_server {
   polar_server_config cfg;
+  Ring pr;
   std::vector<Slot> slots;
   std::deque<Pending> queue;
   std::unordered_map<uint64_t, Record> records;
@@ -160,13 +195,249 @@ void scheduler(polar_server *s, size_t first, size_t step) {
   }
 }
 
+// ---------------------------------------------------------------- persistent
+void finish_ticket(polar_server *s, uint64_t ticket, int status) {
+  auto it = s->records.find(ticket);
+  if (it != s->records.end()) {
+    it->second.status = status;
+    it->second.t_done = Clock::now();
+  }
+  s->completed++;
+  s->cv_done.notify_all();
+}
+
+// Completions: every published frame whose completion word has arrived.
+void ring_collect(polar_server *s) {
+  Ring &r = s->pr;
+  for (uint32_t idx : r.out) {
+    const uint32_t e = idx & (r.R - 1);
+    if (r.seen[e]) continue;
+    if (__atomic_load_n(r.done + e, __ATOMIC_ACQUIRE) != idx + 1) continue;
+    r.seen[e] = 1;
+    auto it = r.left.find(r.ticket[e]);
+    if (it != r.left.end() && --it->second == 0) {
+      finish_ticket(s, it->first, POLAR_OK);
+      r.left.erase(it);
+    }
+  }
+  while (!r.out.empty() && r.seen[r.out.front() & (r.R - 1)]) r.out.pop_front();
+}
+
+// Publishes the oldest pending requests while the ring has room.
+void ring_publish(polar_server *s) {
+  Ring &r = s->pr;
+  int dev = s->cfg.device;
+  while (!s->queue.empty()) {
+    Pending &p = s->queue.front();
+    const uint32_t nf = (uint32_t)p.req.nframes;
+    const uint32_t oldest = r.out.empty() ? r.published : r.out.front();
+    if (r.published + nf - oldest > r.R) break;           // ring full
+    polar_frozen_set *fs = const_cast<polar_frozen_set *>(p.req.fs);
+    const int n = (int)fs->log2n, t = std::min(n, r.t);
+    cudaError_t e = cudaSuccess;
+    const uint32_t *mask = polar::device_mask(fs, dev, &e);
+    const uint32_t *cls = mask && t >= 5 ? polar::device_class_table(fs, dev, t, &e) : nullptr;
+    const uint32_t *ucls =
+        mask && n > t ? polar::device_upper_class_table(fs, dev, t, &e) : nullptr;
+    if (!mask || (t >= 5 && !cls) || (n > t && !ucls)) {
+      polar::set_last_error(cudaGetErrorString(e));
+      finish_ticket(s, p.ticket, e == cudaErrorMemoryAllocation ? POLAR_ENOMEM : POLAR_ECUDA);
+      s->queue.pop_front();
+      continue;
+    }
+    const uint64_t N = uint64_t(1) << n;
+    const size_t W = fs->mask.size();
+    for (uint32_t f = 0; f < nf; ++f) {
+      const uint32_t idx = r.published + f, ent = idx & (r.R - 1);
+      polar::PFrame &d = r.ring[ent];
+      d.llr = p.req.llr + f * N;
+      d.fv = p.req.frozen_vals + f * W;
+      d.xhat = p.req.xhat + f * W;
+      d.uhat = p.req.uhat ? p.req.uhat + f * W : nullptr;
+      d.mask = mask;
+      d.cls = cls;
+      d.ucls = ucls;
+      d.log2n = (uint32_t)n;
+      d.t = (uint32_t)t;
+      r.seen[ent] = 0;
+      r.ticket[ent] = p.ticket;
+      r.out.push_back(idx);
+    }
+    r.left[p.ticket] = (int)nf;
+    r.published += nf;
+    __atomic_store_n(r.ctl, r.published, __ATOMIC_RELEASE);   // tail
+    auto it = s->records.find(p.ticket);
+    if (it != s->records.end()) it->second.t_launch = Clock::now();
+    s->launched++;
+    s->queue.pop_front();
+  }
+}
+
+// (Re)launches the decoder when frames wait and no launch is running; asks a
+// running launch to end (stop word) once nothing has been outstanding for a
+// millisecond.  The launch's own 50 ms idle limit only bounds its waits.
+int ring_launch(polar_server *s) {
+  Ring &r = s->pr;
+  const Clock::time_point now = Clock::now();
+  if (!r.out.empty() || !s->queue.empty()) r.last_busy = now;
+  if (r.running) {
+    const cudaError_t q = cudaEventQuery(r.ev);
+    if (q == cudaErrorNotReady) {
+      if (!r.stopping && r.out.empty() && s->queue.empty() &&
+          now - r.last_busy > std::chrono::milliseconds(1)) {
+        __atomic_store_n(r.ctl + 1, 1u, __ATOMIC_RELEASE);
+        r.stopping = true;
+      }
+      return POLAR_OK;
+    }
+    r.running = false;
+    if (q != cudaSuccess) {
+      polar::set_last_error(cudaGetErrorString(q));
+      return POLAR_ECUDA;
+    }
+    ring_collect(s);                        // words written by the launch that ended
+  }
+  if (r.out.empty()) return POLAR_OK;
+  if (r.stopping) {                         // the ended launch no longer reads it
+    __atomic_store_n(r.ctl + 1, 0u, __ATOMIC_RELEASE);
+    r.stopping = false;
+  }
+  polar::ServeArgs a;
+  a.ring = r.ring;
+  a.rmask = r.R - 1;
+  a.tail = r.ctl;
+  a.stop = r.ctl + 1;
+  a.done = r.done;
+  a.head = r.head;
+  a.scratch = r.scratch;
+  a.cta_floats = r.cta_floats;
+  a.idle_ns = 50000000;
+  a.S = 0;
+  cudaError_t e = polar::launch_serve((int)s->cfg.fkind, a, r.t, r.grid, r.stream);
+  if (e == cudaSuccess) e = cudaEventRecord(r.ev, r.stream);
+  if (e != cudaSuccess) {
+    polar::set_last_error(cudaGetErrorString(e));
+    return POLAR_ECUDA;
+  }
+  r.running = true;
+  return POLAR_OK;
+}
+
+// Every published frame and every pending request fails with `status`.
+void ring_fail_all(polar_server *s, int status) {
+  Ring &r = s->pr;
+  for (auto &kv : r.left) finish_ticket(s, kv.first, status);
+  r.left.clear();
+  r.out.clear();
+  while (!s->queue.empty()) {
+    finish_ticket(s, s->queue.front().ticket, status);
+    s->queue.pop_front();
+  }
+}
+
+void ring_scheduler(polar_server *s) {
+  cudaSetDevice(s->cfg.device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  bool failed = false;
+  while (true) {
+    if (!failed) {
+      ring_collect(s);
+      ring_publish(s);
+      if (ring_launch(s) != POLAR_OK) {
+        failed = true;
+        ring_fail_all(s, POLAR_ECUDA);
+      }
+    } else if (!s->queue.empty()) {
+      ring_fail_all(s, POLAR_ECUDA);
+    }
+    const bool busy = !s->pr.out.empty();
+    if (s->stop && s->queue.empty() && !busy) break;
+    if (busy) {
+      lk.unlock();
+      std::this_thread::sleep_for(std::chrono::microseconds(5));
+      lk.lock();
+    } else {
+      s->cv_done.wait_for(lk, std::chrono::microseconds(200));
+    }
+  }
+  __atomic_store_n(s->pr.ctl + 1, 1u, __ATOMIC_RELEASE);      // stop: idle CTAs leave
+}
+
+void ring_release(polar_server *s) {
+  Ring &r = s->pr;
+  if (r.stream) cudaStreamSynchronize(r.stream);
+  if (r.ev) cudaEventDestroy(r.ev);
+  if (r.stream) cudaStreamDestroy(r.stream);
+  if (r.head) cudaFree(r.head);
+  if (r.scratch) cudaFree(r.scratch);
+  if (r.ring) cudaFreeHost(r.ring);
+  if (r.ctl) cudaFreeHost(r.ctl);
+  r = Ring();
+}
+
+int ring_create(polar_server *s) {
+  Ring &r = s->pr;
+  const polar_server_config &c = s->cfg;
+  long tcfg = 13;
+  polar_config_get("subtree_log2", &tcfg);
+  r.t = (int)tcfg;
+  const int nmax = c.max_log2n ? c.max_log2n : 22;
+  const int per_sm = polar::serve_ctas_per_sm((int)c.fkind, r.t);
+  int sms = 0;
+  if (per_sm < 1 || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device) !=
+                        cudaSuccess) {
+    cudaGetLastError();
+    return POLAR_ECUDA;
+  }
+  r.cta_floats = nmax > r.t ? (uint64_t(1) << nmax) - (uint64_t(1) << r.t) : 0;
+  r.cta_floats = (r.cta_floats + 63) & ~uint64_t(63);
+  uint64_t fit = r.cta_floats ? c.mem_budget / (r.cta_floats * sizeof(float)) : ~uint64_t(0);
+  r.grid = (int)std::min<uint64_t>({(uint64_t)per_sm * sms, (uint64_t)c.max_inflight, fit});
+  if (r.grid < 1) return POLAR_ENOMEM;
+  r.R = 1024;
+  while (r.R < 4u * (uint32_t)r.grid) r.R *= 2;
+  r.seen.assign(r.R, 1);
+  r.ticket.assign(r.R, 0);
+  auto fail = [&](cudaError_t e) {
+    polar::set_last_error(cudaGetErrorString(e));
+    cudaGetLastError();
+    ring_release(s);
+    return e == cudaErrorMemoryAllocation ? POLAR_ENOMEM : POLAR_ECUDA;
+  };
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&r.stream, cudaStreamNonBlocking)) != cudaSuccess) return fail(e);
+  if ((e = cudaEventCreateWithFlags(&r.ev, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
+  if ((e = cudaHostAlloc(reinterpret_cast<void **>(&r.ring), r.R * sizeof(polar::PFrame),
+                         cudaHostAllocMapped | cudaHostAllocPortable)) != cudaSuccess)
+    return fail(e);
+  if ((e = cudaHostAlloc(reinterpret_cast<void **>(&r.ctl), (64 + r.R) * sizeof(uint32_t),
+                         cudaHostAllocMapped | cudaHostAllocPortable)) != cudaSuccess)
+    return fail(e);
+  std::memset(r.ctl, 0, (64 + r.R) * sizeof(uint32_t));
+  r.done = r.ctl + 64;
+  if ((e = cudaMalloc(reinterpret_cast<void **>(&r.head), 256)) != cudaSuccess) return fail(e);
+  if ((e = cudaMemset(r.head, 0, 256)) != cudaSuccess) return fail(e);
+  if (r.cta_floats &&
+      (e = cudaMalloc(reinterpret_cast<void **>(&r.scratch),
+                      (size_t)r.grid * r.cta_floats * sizeof(float))) != cudaSuccess)
+    return fail(e);
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e);
+  s->ws_total = (size_t)r.grid * r.cta_floats * sizeof(float);
+  return POLAR_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
 int polar_server_create(const polar_server_config *cfg, polar_server **out) {
   if (!cfg || !out) return POLAR_EINVAL;
-  if (cfg->max_inflight < 1 || cfg->max_inflight > 256 || cfg->max_queue < 1) return POLAR_EINVAL;
+  if (cfg->persistent != 0 && cfg->persistent != 1) return POLAR_EINVAL;
+  if (cfg->max_inflight < 1 || cfg->max_inflight > (cfg->persistent ? 4096 : 256) ||
+      cfg->max_queue < 1)
+    return POLAR_EINVAL;
+  if (cfg->persistent && (cfg->prec != POLAR_FP32 || cfg->max_log2n < 0 || cfg->max_log2n > 26))
+    return POLAR_EINVAL;
   if (cfg->fkind != POLAR_F_MINSUM && cfg->fkind != POLAR_F_EXACT) return POLAR_EINVAL;
   if (cfg->prec != POLAR_FP32 && cfg->prec != POLAR_FP16 && cfg->prec != POLAR_INT8)
     return POLAR_EINVAL;
@@ -182,6 +453,17 @@ int polar_server_create(const polar_server_config *cfg, polar_server **out) {
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(cfg->device);
+  if (cfg->persistent) {
+    const int rc = ring_create(s);
+    cudaSetDevice(prev);
+    if (rc != POLAR_OK) {
+      delete s;
+      return rc;
+    }
+    s->threads.emplace_back(ring_scheduler, s);
+    *out = s;
+    return POLAR_OK;
+  }
   s->slots.resize(cfg->max_inflight);
   for (auto &sl : s->slots) {
     if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -207,6 +489,10 @@ int polar_server_submit(polar_server *s, const polar_request *req, uint64_t *tic
   if (!s || !ticket) return POLAR_EINVAL;
   int rc = check_request(req);
   if (rc) return rc;
+  if (s->cfg.persistent) {
+    const int nmax = s->cfg.max_log2n ? s->cfg.max_log2n : 22;
+    if ((int)req->fs->log2n > nmax || (uint32_t)req->nframes > s->pr.R / 2) return POLAR_EINVAL;
+  }
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->stop) return POLAR_EINVAL;
   if ((int)s->queue.size() >= s->cfg.max_queue) {
@@ -276,6 +562,7 @@ void polar_server_destroy(polar_server *s) {
   s->cv_done.notify_all();
   for (auto &th : s->threads)
     if (th.joinable()) th.join();
+  if (s->cfg.persistent) ring_release(s);
   for (auto &sl : s->slots) {
     cudaStreamSynchronize(sl.stream);
     polar::release_stream_workspace(s->cfg.device, sl.stream);

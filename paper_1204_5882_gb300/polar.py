@@ -40,7 +40,7 @@ class PolarError(RuntimeError):
 class ServerConfig(C.Structure):
     _fields_ = [("device", C.c_int), ("max_inflight", C.c_int), ("max_queue", C.c_int),
                 ("mem_budget", C.c_size_t), ("fkind", C.c_int), ("prec", C.c_int),
-                ("threads", C.c_int)]
+                ("threads", C.c_int), ("persistent", C.c_int), ("max_log2n", C.c_int)]
 
 
 class Request(C.Structure):
@@ -297,9 +297,10 @@ class Server:
     """Owner of a library request server (destroyed on close / collection)."""
 
     def __init__(self, device=0, max_inflight=32, max_queue=4096, mem_budget=8 << 30,
-                 fkind="minsum", prec="fp32", threads=0):
+                 fkind="minsum", prec="fp32", threads=0, persistent=False, max_log2n=0):
         cfg = ServerConfig(int(device), int(max_inflight), int(max_queue), int(mem_budget),
-                           FKIND[fkind], PREC[prec], int(threads))
+                           FKIND[fkind], PREC[prec], int(threads), int(bool(persistent)),
+                           int(max_log2n))
         h = C.c_void_p()
         _check("polar_server_create", _lib.polar_server_create(C.byref(cfg), C.byref(h)))
         self.handle = h

@@ -124,7 +124,11 @@ def test_server_config_rejected_on_host(P):
     for cfg in (P.ServerConfig(0, 0, 16, 1 << 30, 0, 0, 0), P.ServerConfig(0, 4, 0, 1 << 30, 0, 0, 0),
                 P.ServerConfig(0, 4, 16, 1 << 30, 5, 0, 0), P.ServerConfig(0, 4, 16, 1 << 30, 0, 7, 0),
                 P.ServerConfig(0, 4, 16, 1 << 30, 0, 0, 99),
-                P.ServerConfig(-1, 4, 16, 1 << 30, 0, 0, 0)):
+                P.ServerConfig(-1, 4, 16, 1 << 30, 0, 0, 0),
+                P.ServerConfig(0, 4, 16, 1 << 30, 0, 1, 0, 1, 0),      # persistent needs fp32
+                P.ServerConfig(0, 4, 16, 1 << 30, 0, 0, 0, 1, 27),     # max_log2n range
+                P.ServerConfig(0, 5000, 16, 1 << 30, 0, 0, 0, 1, 0),   # resident CTA cap
+                P.ServerConfig(0, 4, 16, 1 << 30, 0, 0, 0, 2, 0)):
         assert P.lib().polar_server_create(C.byref(cfg), C.byref(h)) == P.POLAR_EINVAL
     assert P.lib().polar_server_submit(None, None, None) == P.POLAR_EINVAL
     assert P.lib().polar_server_poll(None, 1, None) == P.POLAR_EINVAL

@@ -55,7 +55,8 @@ def make_requests(P, count, seed, sizes=(10, 12, 14, 16)):
 
 
 @pytest.mark.gpu
-def test_results_identical_alone_and_in_mix(P):
+@pytest.mark.parametrize("persistent", [False, True])
+def test_results_identical_alone_and_in_mix(P, persistent):
     reqs = make_requests(P, 40, 11)
     stream = torch.cuda.Stream()
     alone = []
@@ -65,7 +66,7 @@ def test_results_identical_alone_and_in_mix(P):
                                stream)
         stream.synchronize()
         alone.append(xh.cpu())
-    srv = P.Server(max_inflight=16, max_queue=1024)
+    srv = P.Server(max_inflight=16, max_queue=1024, persistent=persistent, max_log2n=16)
     outs, tickets = [], []
     for r in reqs:
         outs.append(torch.full_like(r["fv"], -1))
@@ -147,3 +148,82 @@ def test_bounded_wait_and_bad_tickets(P):
     with pytest.raises(P.PolarError):
         srv.poll(987654321)
     srv.close()
+
+
+# ------------------------------------------------------------------ persistent mode
+def alone_results(P, reqs):
+    stream = torch.cuda.Stream()
+    out = []
+    for r in reqs:
+        xh = torch.zeros_like(r["fv"])
+        P.polar_sc_decode_many(r["fs"], r["F"], r["llr"], r["fv"], xh, None, "minsum", "fp32",
+                               stream)
+        stream.synchronize()
+        out.append(xh.cpu())
+    return out
+
+
+@pytest.mark.gpu
+def test_persistent_server_admits_while_running(P):
+    """Requests submitted in waves while earlier ones decode join the running
+    launch: results equal the alone results, and the server makes far fewer
+    launches than requests."""
+    import time
+    reqs = make_requests(P, 60, 21, sizes=(10, 12, 14, 16, 18))
+    alone = alone_results(P, reqs)
+    srv = P.Server(max_inflight=64, max_queue=1024, persistent=True, max_log2n=18)
+    outs = [torch.full_like(r["fv"], -1) for r in reqs]
+    torch.cuda.synchronize()
+    before = P.polar_kernel_launches()
+    tickets = []
+    for w in range(6):                               # six waves, 10 requests each
+        for r, xh in list(zip(reqs, outs))[10 * w:10 * w + 10]:
+            t = srv.submit(r["fs"], r["F"], r["llr"], r["fv"], xh)
+            assert t is not None
+            tickets.append(t)
+        time.sleep(0.0003)
+    for t in tickets:
+        st, q_ms, lat_ms = srv.wait(t, 60000.0)
+        assert st == P.POLAR_OK and lat_ms >= q_ms >= 0.0
+    launches = P.polar_kernel_launches() - before
+    stats = srv.stats()
+    srv.close()
+    assert stats["completed"] == len(reqs) and stats["launched"] == len(reqs)
+    assert 1 <= launches < len(reqs)
+    for a, b in zip(alone, outs):
+        assert torch.equal(a, b.cpu())
+
+
+@pytest.mark.gpu
+def test_persistent_server_relaunches_after_idle(P):
+    """The resident launch ends after a quiet millisecond; a later request
+    starts a new one and completes."""
+    import time
+    reqs = make_requests(P, 3, 22, sizes=(12, 16))
+    alone = alone_results(P, reqs)
+    srv = P.Server(max_inflight=8, persistent=True, max_log2n=16)
+    outs = [torch.full_like(r["fv"], -1) for r in reqs]
+    torch.cuda.synchronize()
+    before = P.polar_kernel_launches()
+    for r, xh in zip(reqs, outs):
+        t = srv.submit(r["fs"], r["F"], r["llr"], r["fv"], xh)
+        assert srv.wait(t, 60000.0)[0] == P.POLAR_OK
+        time.sleep(0.02)                             # well past the idle limit
+    assert P.polar_kernel_launches() - before == len(reqs)
+    srv.close()
+    for a, b in zip(alone, outs):
+        assert torch.equal(a, b.cpu())
+
+
+@pytest.mark.gpu
+def test_persistent_server_refuses_long_codes_and_huge_requests(P):
+    r = make_requests(P, 1, 23, sizes=(16,))[0]
+    srv = P.Server(max_inflight=4, persistent=True, max_log2n=14)
+    xh = torch.zeros_like(r["fv"])
+    with pytest.raises(P.PolarError) as e:
+        srv.submit(r["fs"], r["F"], r["llr"], r["fv"], xh)
+    assert e.value.status == P.POLAR_EINVAL
+    srv.close()
+    with pytest.raises(P.PolarError) as e:             # scratch of one CTA over budget
+        P.Server(max_inflight=4, persistent=True, max_log2n=22, mem_budget=1 << 20)
+    assert e.value.status == P.POLAR_ENOMEM
