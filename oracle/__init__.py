@@ -67,6 +67,10 @@ def lib():
         L.or_ln_q.argtypes = [C.c_double]
         L.or_ln_q.restype = C.c_double
         L.or_select_frozen.argtypes = [C.c_int, P, C.c_uint64, P]
+        L.or_tv_pe.argtypes = [C.c_int, C.c_int, C.c_double, C.c_int, P]
+        L.or_tv_pe.restype = C.c_int
+        L.or_k_for_sum.argtypes = [C.c_int, P, C.c_double]
+        L.or_k_for_sum.restype = C.c_uint64
         L.or_capacity_bsc.argtypes = [C.c_double]
         L.or_capacity_bsc.restype = C.c_double
         L.or_capacity_biawgn.argtypes = [C.c_double]
@@ -219,6 +223,32 @@ def select_frozen(bad, K: int) -> np.ndarray:
     fz = np.empty(bad.size, dtype=np.uint8)
     lib().or_select_frozen(log2_of(bad.size), _p(bad), int(K), _p(fz))
     return fz
+
+
+def tv_pe(n: int, channel: str, param: float, mu: int = 16) -> np.ndarray:
+    """Upper bounds on every bit-channel's ML error probability from the
+    degraded (Tal-Vardy) construction with mu output symbols per channel."""
+    out = np.empty(1 << n, dtype=np.float64)
+    rc = lib().or_tv_pe(n, 0 if channel == "bsc" else 1, float(param), int(mu), _p(out))
+    if rc:
+        raise ValueError((n, channel, param, mu))
+    return out
+
+
+def k_for_sum(bad, target: float) -> int:
+    """Largest K whose K most reliable entries of `bad` sum to <= target."""
+    bad = np.ascontiguousarray(np.asarray(bad, dtype=np.float64))
+    return int(lib().or_k_for_sum(log2_of(bad.size), _p(bad), float(target)))
+
+
+def frozen_set_tv(n: int, channel: str, param: float, rate: float = 0.0,
+                  sum_pe_max: float = 0.1, mu: int = 16):
+    """(frozen mask, K, sum of P_e over the information set) of the degraded
+    construction; K = floor(rate * N) if rate > 0, else the Sec. 3 rule."""
+    pe = tv_pe(n, channel, param, mu)
+    K = int(math.floor(rate * (1 << n))) if rate > 0 else k_for_sum(pe, sum_pe_max)
+    fz = select_frozen(pe, K)
+    return fz, K, float(pe[fz == 0].sum())
 
 
 def unreliability(n: int, channel: str, param: float) -> np.ndarray:

@@ -406,6 +406,226 @@ OR_API void or_select_frozen(int n, const double *bad, uint64_t K, uint8_t *froz
 }
 
 /* ------------------------------------------------------------------------ */
+/* Degraded-channel construction: the density evolution of Sec. 3 made      */
+/* finite (Tal & Vardy, "How to construct polar codes", IEEE Trans. IT      */
+/* 2013, degrading merge).  A symmetric binary-input channel is held as at  */
+/* most M conjugate output pairs (a, b), a >= b: a = W(y|0) = W(y'|1) and   */
+/* b = W(y|1) = W(y'|0), y' the conjugate output; the pairs' a + b sum to 1 */
+/* and the ML error probability is sum b.  With W^-(y1,y2|u1) =             */
+/* 1/2 sum_u2 W(y1|u1^u2) W(y2|u2) and W^+(y1,y2,u1|u2) = 1/2 W(y1|u1^u2)   */
+/* W(y2|u2), the outputs built from pairs i <= j of W group into:           */
+/*   minus: (a_i a_j + b_i b_j, a_i b_j + b_i a_j)                          */
+/*   plus:  (a_i a_j, b_i b_j) and (max, min)(a_i b_j, b_i a_j)             */
+/* each counted twice when i < j (the orders (i, j) and (j, i)).  The pairs */
+/* are then sorted by likelihood ratio a/b and, while more than M remain,   */
+/* the two neighbours whose merger (a1+a2, b1+b2) loses the least mutual    */
+/* information are merged (first such neighbour in ratio order on ties).    */
+/* Merging outputs degrades the channel, so sum b of each bit-channel is an */
+/* upper bound on its true error probability that tightens as M grows; with */
+/* no merge it is exact.  Index convention as above: the first polarisation */
+/* step is the most significant index bit.                                  */
+/* BI-AWGN start: y >= 0 is cut into M0 intervals of equal capacity         */
+/* contribution (in the LLR 2y/sigma^2), giving pairs                       */
+/*   a = P(y in I | +1), b = P(y in I | -1) = P(-y in I | +1),              */
+/* then merged down to M like any other step.                               */
+/* ------------------------------------------------------------------------ */
+typedef struct { double a, b; } tv_pair;
+
+static double tv_info(tv_pair p) /* bits carried by a pair (a + b of them) */
+{
+    double s = p.a + p.b, r = 0.0;
+    if (p.a > 0.0) r += p.a * log2(2.0 * p.a / s);
+    if (p.b > 0.0) r += p.b * log2(2.0 * p.b / s);
+    return r;
+}
+
+static int tv_cmp(const void *pa, const void *pb) /* a/b ascending, then a, then b */
+{
+    const tv_pair *x = (const tv_pair *)pa, *y = (const tv_pair *)pb;
+    double l = x->a * y->b, r = y->a * x->b;
+    if (l != r) return l < r ? -1 : 1;
+    if (x->a != y->a) return x->a < y->a ? -1 : 1;
+    if (x->b != y->b) return x->b < y->b ? -1 : 1;
+    return 0;
+}
+
+/* Drops empty pairs, sorts, merges down to at most M pairs; returns the     */
+/* count.  info[] caches each pair's information, loss[k] that of merging    */
+/* pairs k and k+1 (only the neighbours of a merger change).                 */
+static int tv_reduce(tv_pair *p, int L, int M, double *info, double *loss)
+{
+    int c = 0;
+    for (int k = 0; k < L; k++)
+        if (p[k].a + p[k].b > 0.0) p[c++] = p[k];
+    L = c;
+    qsort(p, (size_t)L, sizeof(tv_pair), tv_cmp);
+    if (L <= M) return L;
+    for (int k = 0; k < L; k++) info[k] = tv_info(p[k]);
+    for (int k = 0; k + 1 < L; k++) {
+        tv_pair m = {p[k].a + p[k + 1].a, p[k].b + p[k + 1].b};
+        loss[k] = info[k] + info[k + 1] - tv_info(m);
+    }
+    while (L > M) {
+        int best = 0;
+        for (int k = 1; k + 1 < L; k++)
+            if (loss[k] < loss[best]) best = k;
+        p[best].a += p[best + 1].a;
+        p[best].b += p[best + 1].b;
+        info[best] = tv_info(p[best]);
+        for (int k = best + 1; k + 1 < L; k++) {
+            p[k] = p[k + 1];
+            info[k] = info[k + 1];
+        }
+        for (int k = best + 1; k + 2 < L; k++) loss[k] = loss[k + 1];
+        L--;
+        for (int k = best - 1; k <= best; k++) {
+            if (k < 0 || k + 1 >= L) continue;
+            tv_pair m = {p[k].a + p[k + 1].a, p[k].b + p[k + 1].b};
+            loss[k] = info[k] + info[k + 1] - tv_info(m);
+        }
+    }
+    return L;
+}
+
+static int tv_minus(const tv_pair *w, int L, tv_pair *out)
+{
+    int c = 0;
+    for (int i = 0; i < L; i++)
+        for (int j = i; j < L; j++) {
+            double f = (i == j) ? 1.0 : 2.0;
+            out[c].a = f * (w[i].a * w[j].a + w[i].b * w[j].b);
+            out[c].b = f * (w[i].a * w[j].b + w[i].b * w[j].a);
+            c++;
+        }
+    return c;
+}
+
+static int tv_plus(const tv_pair *w, int L, tv_pair *out)
+{
+    int c = 0;
+    for (int i = 0; i < L; i++)
+        for (int j = i; j < L; j++) {
+            double f = (i == j) ? 1.0 : 2.0;
+            double x = w[i].a * w[j].b, y = w[i].b * w[j].a;
+            out[c].a = f * w[i].a * w[j].a;
+            out[c].b = f * w[i].b * w[j].b;
+            c++;
+            out[c].a = f * (x > y ? x : y);
+            out[c].b = f * (x > y ? y : x);
+            c++;
+        }
+    return c;
+}
+
+/* Capacity contribution 1 - h2(1 / (1 + e^l)) of an output with LLR l >= 0. */
+static double tv_cap_llr(double l)
+{
+    double q = 1.0 / (1.0 + exp(l));
+    if (q <= 0.0) return 1.0;
+    return 1.0 + q * log2(q) + (1.0 - q) * log2(1.0 - q);
+}
+
+static double tv_q(double x) { return 0.5 * erfc(x / M_SQRT2); }
+
+/* Starting channel: returns its pair count (at most M0 before merging). */
+static int tv_start(int channel, double param, int M0, tv_pair *p)
+{
+    if (channel == 0) { /* BSC(p) */
+        p[0].a = 1.0 - param;
+        p[0].b = param;
+        return 1;
+    }
+    double s2 = param, sg = sqrt(param);
+    double lo_y = 0.0;
+    for (int k = 0; k < M0; k++) {
+        double hi_y;
+        if (k + 1 == M0) {
+            hi_y = INFINITY;
+        } else { /* LLR where the capacity contribution reaches (k+1)/M0 */
+            double target = (double)(k + 1) / M0, lo = 0.0, hi = 1.0;
+            while (tv_cap_llr(hi) < target) hi *= 2.0;
+            for (int it = 0; it < 200; it++) {
+                double mid = 0.5 * (lo + hi);
+                if (mid <= lo || mid >= hi) break;
+                if (tv_cap_llr(mid) < target) lo = mid; else hi = mid;
+            }
+            hi_y = hi * s2 / 2.0;
+        }
+        double qa_hi = isinf(hi_y) ? 0.0 : tv_q((hi_y - 1.0) / sg);
+        double qb_hi = isinf(hi_y) ? 0.0 : tv_q((hi_y + 1.0) / sg);
+        p[k].a = tv_q((lo_y - 1.0) / sg) - qa_hi;
+        p[k].b = tv_q((lo_y + 1.0) / sg) - qb_hi;
+        lo_y = hi_y;
+    }
+    return M0;
+}
+
+/* Upper bounds on the ML error probability of every bit-channel of a code  */
+/* of length 2^n on the BSC (channel 0, param = p) or the BI-AWGN channel   */
+/* (channel 1, param = sigma^2), with at most M = mu / 2 pairs per channel. */
+/* Returns 0, or -1 for a bad argument.                                     */
+OR_API int or_tv_pe(int n, int channel, double param, int mu, double *pe)
+{
+    int M = mu / 2, M0 = 4 * M;
+    if (n < 0 || n > 24 || M < 1 || M > 64 || (channel != 0 && channel != 1)) return -1;
+    size_t N = (size_t)1 << n;
+    int cap = 2 * M * (M + 1) > M0 ? 2 * M * (M + 1) : M0;
+    tv_pair *cur = (tv_pair *)malloc(sizeof(tv_pair) * N * M);
+    tv_pair *nxt = (tv_pair *)malloc(sizeof(tv_pair) * N * M);
+    int *cnt = (int *)malloc(sizeof(int) * N), *ncnt = (int *)malloc(sizeof(int) * N);
+    tv_pair *tmp = (tv_pair *)malloc(sizeof(tv_pair) * cap);
+    double *info = (double *)malloc(sizeof(double) * cap);
+    double *loss = (double *)malloc(sizeof(double) * cap);
+    int L0 = tv_start(channel, param, M0, tmp);
+    cnt[0] = tv_reduce(tmp, L0, M, info, loss);
+    memcpy(cur, tmp, sizeof(tv_pair) * cnt[0]);
+    for (int s = 0; s < n; s++) {
+        size_t len = (size_t)1 << s;
+        for (size_t j = 0; j < len; j++) {
+            for (int side = 0; side < 2; side++) {
+                int L = side == 0 ? tv_minus(cur + j * M, cnt[j], tmp)
+                                  : tv_plus(cur + j * M, cnt[j], tmp);
+                L = tv_reduce(tmp, L, M, info, loss);
+                memcpy(nxt + (2 * j + side) * M, tmp, sizeof(tv_pair) * L);
+                ncnt[2 * j + side] = L;
+            }
+        }
+        tv_pair *t = cur; cur = nxt; nxt = t;
+        int *tc = cnt; cnt = ncnt; ncnt = tc;
+    }
+    for (size_t i = 0; i < N; i++) {
+        double e = 0.0;
+        for (int k = 0; k < cnt[i]; k++) e += cur[i * M + k].b;
+        pe[i] = e;
+    }
+    free(cur); free(nxt); free(cnt); free(ncnt); free(tmp); free(info); free(loss);
+    return 0;
+}
+
+/* Sec. 3's rule for the code rate: the frame error rate of SC is at most   */
+/* the sum of the information bits' error probabilities, so K is the        */
+/* largest count whose most reliable bit-channels sum to at most `target`.  */
+/* Reliability order as in or_select_frozen (bad descending, lower index     */
+/* first on ties, so the information set is the tail of that order).        */
+OR_API uint64_t or_k_for_sum(int n, const double *bad, double target)
+{
+    size_t N = (size_t)1 << n;
+    uint32_t *idx = (uint32_t *)malloc(sizeof(uint32_t) * N);
+    for (size_t i = 0; i < N; i++) idx[i] = (uint32_t)i;
+    g_bad = bad;
+    qsort(idx, N, sizeof(uint32_t), cmp_unrel);
+    double acc = 0.0;
+    uint64_t K = 0;
+    for (size_t r = N; r-- > 0;) {
+        acc += bad[idx[r]];
+        if (acc > target) break;
+        K++;
+    }
+    free(idx);
+    return K;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Capacities for the efficiency beta = R / C (Sec. 2.1, Eq. 3).            */
 /* BSC: C = 1 - h2(p).  BIAWGN with x = 0 sent (+1):                        */
 /*   C = 1 - E[log2(1 + exp(-2Y/sigma^2))],  Y ~ N(1, sigma^2),             */

@@ -166,7 +166,7 @@ def _genie_error_rates(n, channel, param, T, seed):
             L = O.llr_biawgn((1.0 - 2.0 * x) + math.sqrt(param) * rng.standard_normal(N), param, 64)
         u = O.encode(x)
         _, _, leaf = O.sc_decode(L, allf, u, "exact", leaf=True)
-        err += ((leaf < 0) != (u == 1)) * 1.0 - 0.5 * (leaf == 0)
+        err += np.where(leaf == 0, 0.5, ((leaf < 0) != (u == 1)) * 1.0)
     return err / T
 
 
