@@ -70,7 +70,9 @@ const char *polar_last_error_string(void);
 /* Process-wide tuning knobs, by name.  Returns POLAR_ENOTFOUND for an
  * unknown key, POLAR_EINVAL for a value out of range.  Keys:
  *   "subtree_log2"  t, log2 of the leaves one CTA decodes in shared memory
- *                   (5..14; default 13); levels above t stream through HBM.
+ *                   (5..14; default 14); levels above t stream through HBM.
+ *   "persist_log2"  the same for the persistent decoder and the persistent
+ *                   server (5..14; default 13, two CTAs per SM).
  *   "shortcuts"     1 = rate-0 / rate-1 node shortcuts (default), 0 = none.
  *   "graphs"        1 = replay batch launch sequences as CUDA graphs
  *                   (default), 0 = launch every kernel eagerly.
@@ -128,6 +130,23 @@ void polar_profile_reset(void);
  * sigma^2 <= 0, rate outside [0, 1], out == NULL. */
 int polar_build_frozen_set(uint32_t log2n, polar_channel ch, double param,
                            double rate, polar_frozen_set **out);
+
+/* Frozen set from the degraded-channel construction (Sec. 3's density
+ * evolution made finite, after Tal & Vardy 2013): every bit-channel is
+ * tracked as a symmetric channel of at most mu outputs (mu even, 2..128),
+ * merged so that it stays degraded with respect to the true bit-channel;
+ * its ML error probability P_e,i is therefore an upper bound that tightens
+ * as mu grows (mu = 16 is within a few percent at N = 2^20).  K =
+ * floor(rate * N) when rate > 0; with rate = 0, Sec. 3's rule: K is the
+ * largest count whose most reliable bit-channels have sum P_e,i <=
+ * sum_pe_max (an upper bound on SC's frame error rate).  The N-K largest
+ * P_e,i are frozen, the lower index first on ties; polar_frozen_set_query
+ * reports the sum over the information set.  Host only, double precision,
+ * all host cores (about 2N mu^2 log mu operations: seconds at 2^20,
+ * a minute at 2^24).  EINVAL as polar_build_frozen_set, or mu out of range,
+ * or sum_pe_max < 0; ENOMEM. */
+int polar_build_frozen_set_tv(uint32_t log2n, polar_channel ch, double param, int mu,
+                              double rate, double sum_pe_max, polar_frozen_set **out);
 
 /* Frozen set from a caller-given mask (bit i set = position i frozen);
  * mask_host holds max(1, N/32) words and is copied. */
@@ -225,7 +244,7 @@ int polar_sc_decode_batch(int nframes, const polar_frame_desc *frames,
 /* Frames of any lengths and frozen sets decoded by ONE persistent launch
  * (Sec. 4's SC recursion, whole frames per CTA).  The frames form a device
  * work queue, longest first; each CTA (four warps; as many per SM as shared
- * memory allows for subtrees of 2^t leaves, t = the "subtree_log2" option)
+ * memory allows for subtrees of 2^t leaves, t = the "persist_log2" option)
  * claims the next frame and decodes it completely: the levels above t
  * stream through a per-CTA slice of the workspace, every 2^t-leaf subtree is
  * decoded in shared memory, rate-0 nodes take beta = fv F^{(x)k}.  Frames

@@ -17,7 +17,8 @@ namespace {
 thread_local std::string g_last_error;
 
 struct Config {
-  std::atomic<long> subtree_log2{13};
+  std::atomic<long> subtree_log2{14};
+  std::atomic<long> persist_log2{13};
   std::atomic<long> shortcuts{1};
   std::atomic<long> graphs{1};
   std::atomic<long> plain{0};
@@ -454,7 +455,7 @@ int decode_persistent(int nframes, const polar_frame_desc *frames, int fkind, in
   int dev = 0;
   int rc = current_device(&dev);
   if (rc) return rc;
-  const int tc = (int)g_cfg.subtree_log2.load();
+  const int tc = (int)g_cfg.persist_log2.load();
   std::vector<int> order(nframes);
   for (int i = 0; i < nframes; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
@@ -624,6 +625,9 @@ int polar_config_set(const char *key, long value) {
   } else if (!strcmp(key, "int8_target")) {
     if (value < 1 || value > 64) return POLAR_EINVAL;
     g_cfg.int8_target = value;
+  } else if (!strcmp(key, "persist_log2")) {
+    if (value < 5 || value > 14) return POLAR_EINVAL;
+    g_cfg.persist_log2 = value;
   } else if (!strcmp(key, "persistent")) {
     if (value < 0 || value > 2) return POLAR_EINVAL;
     g_cfg.persistent = value;
@@ -644,6 +648,7 @@ int polar_config_get(const char *key, long *value) {
   else if (!strcmp(key, "fuse")) *value = g_cfg.fuse;
   else if (!strcmp(key, "autotune")) *value = g_cfg.autotune;
   else if (!strcmp(key, "persistent")) *value = g_cfg.persistent;
+  else if (!strcmp(key, "persist_log2")) *value = g_cfg.persist_log2;
   else return POLAR_ENOTFOUND;
   return POLAR_OK;
 }
@@ -679,6 +684,11 @@ void polar_profile_reset(void) {
 int polar_build_frozen_set(uint32_t log2n, polar_channel ch, double param, double rate,
                            polar_frozen_set **out) {
   return build_frozen_set(log2n, ch, param, rate, out);
+}
+
+int polar_build_frozen_set_tv(uint32_t log2n, polar_channel ch, double param, int mu,
+                              double rate, double sum_pe_max, polar_frozen_set **out) {
+  return build_frozen_set_tv(log2n, ch, param, mu, rate, sum_pe_max, out);
 }
 
 int polar_frozen_set_from_mask(uint32_t log2n, const uint32_t *mask_host,

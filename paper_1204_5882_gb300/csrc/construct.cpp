@@ -189,6 +189,266 @@ int build_frozen_set(uint32_t log2n, polar_channel ch, double param, double rate
   return POLAR_OK;
 }
 
+// ---------------------------------------------------------------- degraded construction
+// Sec. 3's density evolution made finite (Tal & Vardy, "How to construct
+// polar codes", 2013): every bit-channel is held as at most M = mu/2
+// conjugate output pairs (a, b), a >= b (a = W(y|0) = W(y'|1)), degraded
+// with respect to the true bit-channel, so its ML error probability sum b is
+// an upper bound that tightens with mu.  From pairs i <= j of a channel
+// (doubled when i < j, for the orders (i, j) and (j, i)):
+//   minus: (a_i a_j + b_i b_j, a_i b_j + b_i a_j)
+//   plus:  (a_i a_j, b_i b_j) and (max, min)(a_i b_j, b_i a_j).
+// The products are sorted by likelihood ratio and the neighbours whose
+// merger loses the least mutual information are merged (the first such
+// neighbour on ties) until M pairs remain.  The BI-AWGN channel starts as
+// 4M pairs cut from y >= 0 at equal steps of capacity contribution.  The
+// tree is walked depth first from 64 subtree roots, in parallel; every leaf
+// is computed by the same sequence of operations whatever the thread.
+namespace {
+
+struct TvPair {
+  double a, b;
+};
+
+double tv_info(const TvPair &p) {
+  const double s = p.a + p.b;
+  double r = 0.0;
+  if (p.a > 0.0) r += p.a * std::log2(2.0 * p.a / s);
+  if (p.b > 0.0) r += p.b * std::log2(2.0 * p.b / s);
+  return r;
+}
+
+// Likelihood ratio a/b ascending (b = 0 last), then a, then b.
+bool tv_before(const TvPair &x, const TvPair &y) {
+  const double l = x.a * y.b, r = y.a * x.b;
+  if (l != r) return l < r;
+  if (x.a != y.a) return x.a < y.a;
+  return x.b < y.b;
+}
+
+struct TvScratch {
+  std::vector<TvPair> prod;
+  std::vector<double> info, loss;
+  explicit TvScratch(int cap) : prod(cap), info(cap), loss(cap) {}
+};
+
+int tv_reduce(TvPair *p, int L, int M, TvScratch &w) {
+  int c = 0;
+  for (int k = 0; k < L; ++k)
+    if (p[k].a + p[k].b > 0.0) p[c++] = p[k];
+  L = c;
+  std::sort(p, p + L, tv_before);
+  if (L <= M) return L;
+  double *info = w.info.data(), *loss = w.loss.data();
+  for (int k = 0; k < L; ++k) info[k] = tv_info(p[k]);
+  auto merged_loss = [&](int k) {
+    const TvPair m{p[k].a + p[k + 1].a, p[k].b + p[k + 1].b};
+    return info[k] + info[k + 1] - tv_info(m);
+  };
+  for (int k = 0; k + 1 < L; ++k) loss[k] = merged_loss(k);
+  while (L > M) {
+    int best = 0;
+    for (int k = 1; k + 1 < L; ++k)
+      if (loss[k] < loss[best]) best = k;
+    p[best].a += p[best + 1].a;
+    p[best].b += p[best + 1].b;
+    info[best] = tv_info(p[best]);
+    for (int k = best + 1; k + 1 < L; ++k) {
+      p[k] = p[k + 1];
+      info[k] = info[k + 1];
+    }
+    for (int k = best + 1; k + 2 < L; ++k) loss[k] = loss[k + 1];
+    --L;
+    for (int k = std::max(best - 1, 0); k <= best && k + 1 < L; ++k) loss[k] = merged_loss(k);
+  }
+  return L;
+}
+
+int tv_child(const TvPair *w, int L, bool plus, TvPair *out) {
+  int c = 0;
+  for (int i = 0; i < L; ++i)
+    for (int j = i; j < L; ++j) {
+      const double f = (i == j) ? 1.0 : 2.0;
+      if (!plus) {
+        out[c].a = f * (w[i].a * w[j].a + w[i].b * w[j].b);
+        out[c].b = f * (w[i].a * w[j].b + w[i].b * w[j].a);
+        ++c;
+      } else {
+        const double x = w[i].a * w[j].b, y = w[i].b * w[j].a;
+        out[c].a = f * w[i].a * w[j].a;
+        out[c].b = f * w[i].b * w[j].b;
+        ++c;
+        out[c].a = f * (x > y ? x : y);
+        out[c].b = f * (x > y ? y : x);
+        ++c;
+      }
+    }
+  return c;
+}
+
+double tv_cap_llr(double l) {   // 1 - h2(1 / (1 + e^l))
+  const double q = 1.0 / (1.0 + std::exp(l));
+  if (q <= 0.0) return 1.0;
+  return 1.0 + q * std::log2(q) + (1.0 - q) * std::log2(1.0 - q);
+}
+
+double tv_q(double x) { return 0.5 * std::erfc(x / M_SQRT2); }
+
+int tv_start(polar_channel ch, double param, int M0, TvPair *p) {
+  if (ch == POLAR_BSC) {
+    p[0] = TvPair{1.0 - param, param};
+    return 1;
+  }
+  const double s2 = param, sg = std::sqrt(param);
+  double lo_y = 0.0;
+  for (int k = 0; k < M0; ++k) {
+    double hi_y = INFINITY;
+    if (k + 1 < M0) {
+      const double target = (double)(k + 1) / M0;
+      double lo = 0.0, hi = 1.0;
+      while (tv_cap_llr(hi) < target) hi *= 2.0;
+      for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (tv_cap_llr(mid) < target) lo = mid;
+        else hi = mid;
+      }
+      hi_y = hi * s2 / 2.0;
+    }
+    const double qa_hi = std::isinf(hi_y) ? 0.0 : tv_q((hi_y - 1.0) / sg);
+    const double qb_hi = std::isinf(hi_y) ? 0.0 : tv_q((hi_y + 1.0) / sg);
+    p[k].a = tv_q((lo_y - 1.0) / sg) - qa_hi;
+    p[k].b = tv_q((lo_y + 1.0) / sg) - qb_hi;
+    lo_y = hi_y;
+  }
+  return M0;
+}
+
+struct TvTree {
+  int n, M;
+  double *pe;
+};
+
+// Depth-first below node (depth s, index j) whose channel is `w` (L pairs).
+void tv_walk(const TvTree &T, const TvPair *w, int L, int s, uint64_t j,
+             std::vector<TvPair> &stack, TvScratch &sc) {
+  if (s == T.n) {
+    double e = 0.0;
+    for (int k = 0; k < L; ++k) e += w[k].b;
+    T.pe[j] = e;
+    return;
+  }
+  TvPair *child = stack.data() + (size_t)(s + 1) * T.M;
+  for (int side = 0; side < 2; ++side) {
+    int c = tv_child(w, L, side == 1, sc.prod.data());
+    c = tv_reduce(sc.prod.data(), c, T.M, sc);
+    std::copy(sc.prod.begin(), sc.prod.begin() + c, child);
+    tv_walk(T, child, c, s + 1, 2 * j + side, stack, sc);
+  }
+}
+
+}  // namespace
+
+int tv_bit_channel_pe(uint32_t log2n, polar_channel ch, double param, int mu,
+                      std::vector<double> &pe) {
+  const int n = (int)log2n, M = mu / 2, M0 = 4 * M;
+  const int cap = std::max(2 * M * (M + 1), M0);
+  try {
+    pe.assign(size_t(1) << n, 0.0);
+  } catch (...) {
+    return POLAR_ENOMEM;
+  }
+  TvScratch sc0(cap);
+  int L0 = tv_start(ch, param, M0, sc0.prod.data());
+  L0 = tv_reduce(sc0.prod.data(), L0, M, sc0);
+  // breadth first down to d0 levels, then one depth-first walk per root
+  const int d0 = std::min(n, 6);
+  std::vector<TvPair> lv((size_t(1) << d0) * M);
+  std::vector<int> cnt(size_t(1) << d0);
+  std::copy(sc0.prod.begin(), sc0.prod.begin() + L0, lv.begin());
+  cnt[0] = L0;
+  for (int s = 0; s < d0; ++s) {
+    std::vector<TvPair> nx((size_t(2) << s) * M);
+    std::vector<int> nc(size_t(2) << s);
+    for (uint64_t j = 0; j < (uint64_t(1) << s); ++j)
+      for (int side = 0; side < 2; ++side) {
+        int c = tv_child(lv.data() + j * M, cnt[j], side == 1, sc0.prod.data());
+        c = tv_reduce(sc0.prod.data(), c, M, sc0);
+        std::copy(sc0.prod.begin(), sc0.prod.begin() + c, nx.begin() + (2 * j + side) * M);
+        nc[2 * j + side] = c;
+      }
+    std::copy(nx.begin(), nx.end(), lv.begin());
+    std::copy(nc.begin(), nc.end(), cnt.begin());
+  }
+  const TvTree T{n, M, pe.data()};
+  const uint64_t roots = uint64_t(1) << d0;
+  std::atomic<uint64_t> next{0};
+  auto worker = [&] {
+    TvScratch sc(cap);
+    std::vector<TvPair> stack((size_t)(n + 1) * M);
+    for (;;) {
+      const uint64_t r = next.fetch_add(1);
+      if (r >= roots) break;
+      tv_walk(T, lv.data() + r * M, cnt[r], d0, r, stack, sc);
+    }
+  };
+  const unsigned nt = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+  if (n <= 10 || nt == 1) {
+    worker();
+  } else {
+    std::vector<std::thread> th;
+    for (unsigned w = 0; w < nt; ++w) th.emplace_back(worker);
+    for (auto &x : th) x.join();
+  }
+  return POLAR_OK;
+}
+
+int build_frozen_set_tv(uint32_t log2n, polar_channel ch, double param, int mu, double rate,
+                        double sum_pe_max, polar_frozen_set **out) {
+  if (!out || log2n < 1 || log2n > 26 || mu < 2 || mu > 128 || (mu & 1)) return POLAR_EINVAL;
+  if (!(rate >= 0.0 && rate <= 1.0) || !(sum_pe_max >= 0.0)) return POLAR_EINVAL;
+  if (ch == POLAR_BSC) {
+    if (!(param > 0.0 && param < 0.5)) return POLAR_EINVAL;
+  } else if (ch == POLAR_BIAWGN) {
+    if (!(param > 0.0 && std::isfinite(param))) return POLAR_EINVAL;
+  } else {
+    return POLAR_EINVAL;
+  }
+  std::vector<double> pe;
+  int rc = tv_bit_channel_pe(log2n, ch, param, mu, pe);
+  if (rc) return rc;
+  const uint64_t N = uint64_t(1) << log2n;
+  // rank: error probability descending, lower index first on ties
+  std::vector<uint32_t> idx(N);
+  for (uint64_t i = 0; i < N; ++i) idx[i] = (uint32_t)i;
+  std::sort(idx.begin(), idx.end(), [&](uint32_t a, uint32_t b) {
+    if (pe[a] != pe[b]) return pe[a] > pe[b];
+    return a < b;
+  });
+  uint64_t K;
+  if (rate > 0.0) {
+    K = std::min<uint64_t>(N, (uint64_t)std::floor(rate * (double)N));
+  } else {   // Sec. 3: the largest K whose best channels sum to <= sum_pe_max
+    double acc = 0.0;
+    K = 0;
+    for (uint64_t r = N; r-- > 0;) {
+      acc += pe[idx[r]];
+      if (acc > sum_pe_max) break;
+      ++K;
+    }
+  }
+  polar_frozen_set *fs = new_set(log2n);
+  if (!fs) return POLAR_ENOMEM;
+  fs->K = K;
+  const uint64_t nf = N - K;
+  for (uint64_t r = 0; r < nf; ++r) fs->mask[idx[r] >> 5] |= 1u << (idx[r] & 31);
+  double s = 0.0;
+  for (uint64_t r = N; r-- > nf;) s += pe[idx[r]];
+  fs->sum_pe = s;
+  *out = fs;
+  return POLAR_OK;
+}
+
 int frozen_set_from_mask(uint32_t log2n, const uint32_t *mask, polar_frozen_set **out) {
   if (!out || !mask || log2n < 1 || log2n > 26) return POLAR_EINVAL;
   polar_frozen_set *fs = new_set(log2n);

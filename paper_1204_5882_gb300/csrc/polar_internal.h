@@ -75,6 +75,12 @@ namespace polar {
 int build_frozen_set(uint32_t log2n, polar_channel ch, double param, double rate,
                      polar_frozen_set **out);
 int frozen_set_from_mask(uint32_t log2n, const uint32_t *mask, polar_frozen_set **out);
+// Degraded-channel (Tal-Vardy) construction: bit-channel error bounds, and
+// the frozen set they give (K = floor(rate N), or by the sum rule if rate = 0).
+int tv_bit_channel_pe(uint32_t log2n, polar_channel ch, double param, int mu,
+                      std::vector<double> &pe);
+int build_frozen_set_tv(uint32_t log2n, polar_channel ch, double param, int mu, double rate,
+                        double sum_pe_max, polar_frozen_set **out);
 NodeClass node_class_host(const polar_frozen_set *fs, int k, uint64_t o);
 std::shared_ptr<Plan> get_plan(polar_frozen_set *fs, int t, bool shortcuts, bool fuse);
 const uint32_t *device_mask(polar_frozen_set *fs, int device, cudaError_t *err);

@@ -379,7 +379,7 @@ int ring_create(polar_server *s) {
   Ring &r = s->pr;
   const polar_server_config &c = s->cfg;
   long tcfg = 13;
-  polar_config_get("subtree_log2", &tcfg);
+  polar_config_get("persist_log2", &tcfg);
   r.t = (int)tcfg;
   const int nmax = c.max_log2n ? c.max_log2n : 22;
   const int per_sm = polar::serve_ctas_per_sm((int)c.fkind, r.t);

@@ -57,6 +57,9 @@ def test_strerror_and_config(P):
     with pytest.raises(P.PolarError):
         P.polar_config_set("no_such_key", 1)
     assert P.polar_config_get("persistent") == 1
+    assert P.polar_config_get("persist_log2") == 13
+    with pytest.raises(P.PolarError):
+        P.polar_config_set("persist_log2", 4)
     with pytest.raises(P.PolarError):
         P.polar_config_set("persistent", 3)
 
@@ -107,6 +110,22 @@ def test_library_construction_equals_oracle(P, case):
     assert fs.K == K
     assert np.array_equal(S.unpack_bits(fs.mask(), 1 << n), ofz)
     assert fs.sum_pe == pytest.approx(O.fer_bound(n, ch, par, ofz), rel=1e-9)
+
+
+@pytest.mark.parametrize("case", [(3, "bsc", 0.11, 128, 0.5, 0.0), (10, "bsc", 0.03, 16, 0.75, 0.0),
+                                  (12, "bsc", 0.02, 16, 0.0, 0.1), (12, "biawgn", 1.0, 16, 0.44, 0.0),
+                                  (14, "biawgn", 0.8, 8, 0.0, 0.05), (16, "bsc", 0.02, 16, 0.0, 0.1)])
+def test_library_degraded_construction_equals_oracle(P, case):
+    import oracle as O
+    from paper_1204_5882_gb300 import synth as S
+    n, ch, par, mu, rate, smax = case
+    fs = P.polar_build_frozen_set_tv(n, ch, par, mu, rate, smax)
+    fz, K, spe = O.frozen_set_tv(n, ch, par, rate=rate, sum_pe_max=smax, mu=mu)
+    assert fs.K == K
+    assert np.array_equal(S.unpack_bits(fs.mask(), 1 << n), fz)
+    assert fs.sum_pe == pytest.approx(spe, rel=1e-12, abs=1e-300)
+    with pytest.raises(P.PolarError):
+        P.polar_build_frozen_set_tv(n, ch, par, 3, rate, smax)
 
 
 def test_frozen_set_from_mask_roundtrip(P):

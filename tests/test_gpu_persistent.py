@@ -31,7 +31,7 @@ def P():
 
 @pytest.fixture(autouse=True)
 def default_config(P):
-    saved = {k: P.polar_config_get(k) for k in ("subtree_log2", "persistent")}
+    saved = {k: P.polar_config_get(k) for k in ("persist_log2", "persistent")}
     yield
     for k, v in saved.items():
         P.polar_config_set(k, v)
@@ -103,7 +103,7 @@ SPECS = [(n, kind, lk)
 
 @pytest.mark.parametrize("t", [5, 9, 13])
 def test_persistent_mixed_minsum_bitexact(P, t):
-    P.polar_config_set("subtree_log2", t)
+    P.polar_config_set("persist_log2", t)
     rng = np.random.default_rng(100 + t)
     frames, inputs = make_frames(P, rng, SPECS)
     P.polar_sc_decode_persistent(frames)
@@ -115,7 +115,7 @@ def test_persistent_mixed_minsum_bitexact(P, t):
 def test_persistent_rate0_upper_nodes(P, t):
     """Low-rate and front-frozen codes: rate-0 nodes and skipped f / g steps
     above the subtree size."""
-    P.polar_config_set("subtree_log2", t)
+    P.polar_config_set("persist_log2", t)
     rng = np.random.default_rng(7 + t)
     specs = [(16, "low_rate", "gauss"), (15, "front_frozen", "bsc"), (16, "low_rate", "bsc"),
              (12, "front_frozen", "gauss")]
@@ -128,7 +128,7 @@ def test_persistent_rate0_upper_nodes(P, t):
 def test_persistent_queue_longer_than_grid(P):
     """More frames than resident CTAs: CTAs loop over the queue.  Every frame
     equals the launched schedule's result; a sample equals the oracle."""
-    P.polar_config_set("subtree_log2", 9)
+    P.polar_config_set("persist_log2", 9)
     rng = np.random.default_rng(11)
     specs = [(int(rng.choice([10, 11, 12])), "polar", "gauss") for _ in range(700)]
     frames, inputs = make_frames(P, rng, specs, uhat_every=3)
@@ -146,7 +146,7 @@ def test_persistent_queue_longer_than_grid(P):
 
 
 def test_persistent_exact_f_matches_launched(P):
-    P.polar_config_set("subtree_log2", 10)
+    P.polar_config_set("persist_log2", 10)
     rng = np.random.default_rng(23)
     specs = [(n, "polar", "gauss") for n in (9, 12, 14, 15, 12, 10)]
     frames, _ = make_frames(P, rng, specs, uhat_every=1)
@@ -161,7 +161,7 @@ def test_persistent_exact_f_matches_launched(P):
 
 def test_persistent_workload_2_20(P):
     """Eight frames of the 2^20 BSC workload next to four 2^16 frames."""
-    P.polar_config_set("subtree_log2", 13)
+    P.polar_config_set("persist_log2", 13)
     w, w2 = S.WORKLOADS["bsc_p03_n20"], S.WORKLOADS["bsc_p02_n16"]
     frames, expect = [], []
     for wl, count in ((w, 8), (w2, 4)):
