@@ -10,7 +10,7 @@
  *   - recursive SC decoding with the phi-based LLR update (Sec. 4).
  *
  * Conventions shared by every entry point:
- *   - N = 2^log2n, 1 <= log2n <= 26.  Transform x = u F^{(x)n} with
+ *   - N = 2^log2n, 1 <= log2n <= 27.  Transform x = u F^{(x)n} with
  *     F = [[1,0],[1,1]] in natural order (no bit reversal); it is its own
  *     inverse over GF(2).
  *   - Bit vectors are packed little-endian in uint32 words: bit i of a
@@ -78,8 +78,12 @@ const char *polar_last_error_string(void);
  *                   (default), 0 = launch every kernel eagerly.
  *   "plain"         1 = the plain per-frame baseline: frames decoded one
  *                   after another, no shortcuts, no graphs; 0 (default).
- *   "profile"       1 = time every kernel group with CUDA events (eager
- *                   launches, see polar_profile_read); 0 (default).
+ *   "profile"       time every kernel group with CUDA events (see
+ *                   polar_profile_read): 1 = a one-off CUDA-graph replay of
+ *                   the batch's schedule with an event-record node around
+ *                   each group (device times without host launch gaps; eager
+ *                   when "graphs" is 0 or the stream is the legacy default
+ *                   or capturing), 2 = eager launches; 0 (default) = off.
  *   "autotune"      1 = use the schedule polar_autotune found for a batch
  *                   shape (default); 0 = ignore tuned entries.
  *   "fuse"          1 = each streamed f/g step and the f steps continuing it
@@ -101,14 +105,14 @@ int polar_config_get(const char *key, long *value);
  * kernels inside replayed CUDA graphs included. */
 uint64_t polar_kernel_launches(void);
 
-/* Per-kind kernel timing, for profiling.  While the "profile" option is 1,
- * decode and map calls launch eagerly (no graphs) and bracket every kernel
- * group with CUDA events on the launching stream.  polar_profile_read
- * synchronises the recorded events and returns, for one kind ("llr",
- * "stream_f", "stream_g", "subtree", "rate0", "chain", "persist"), the
- * summed device time in ms,
- * the number of launches and the algorithmic bytes those launches move
- * (inputs read once, outputs written once).  polar_profile_reset discards
+/* Per-kind kernel timing, for profiling.  While the "profile" option is
+ * set, decode and map calls bracket every kernel group with CUDA events on
+ * the launching stream (inside a one-off graph replay, or eagerly).
+ * polar_profile_read synchronises the recorded events and returns, for one
+ * kind ("llr", "stream_f", "stream_g", "subtree", "rate0", "chain",
+ * "persist"), the summed device time in ms, the number of launches and the
+ * algorithmic bytes those launches move (inputs read once, outputs written
+ * once).  polar_profile_reset discards
  * what was recorded.  Any pointer may be NULL. */
 int polar_profile_read(const char *kind, double *total_ms, uint64_t *launches,
                        double *alg_bytes);
@@ -126,7 +130,7 @@ void polar_profile_reset(void);
  * P_e = Q(sqrt(m/2)) (BI-AWGN).  Equal reliabilities freeze the lower index
  * first.  Runs on the host in double precision; the device copy is made on
  * first use.  *out receives a library-owned object (free with
- * polar_frozen_set_free).  EINVAL: log2n outside 1..26, p outside (0, 0.5),
+ * polar_frozen_set_free).  EINVAL: log2n outside 1..27, p outside (0, 0.5),
  * sigma^2 <= 0, rate outside [0, 1], out == NULL. */
 int polar_build_frozen_set(uint32_t log2n, polar_channel ch, double param,
                            double rate, polar_frozen_set **out);
@@ -315,7 +319,7 @@ typedef struct {
     int threads;        /* slots: host scheduler threads launching work, 0 = 4;
                            each owns an equal share of the slots */
     int persistent;     /* 1 = persistent mode (prec must be POLAR_FP32) */
-    int max_log2n;      /* persistent: longest code accepted, 1..26, 0 = 22;
+    int max_log2n;      /* persistent: longest code accepted, 1..27, 0 = 22;
                            longer requests are refused at submit (EINVAL) */
 } polar_server_config;
 

@@ -372,13 +372,39 @@ int decode_group(const Group &g, cudaStream_t s, const Opts &opt) {
   }
   Exec x{plan.get(), &g, dmask, ws, n, t, dclass};
   const bool prof = opt.profile;
-  bool use_graph = graphs && !prof && s != nullptr;
+  bool use_graph = graphs && s != nullptr;
   if (use_graph) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     CK(cudaStreamIsCapturing(s, &cs));
     if (cs != cudaStreamCaptureStatusNone) use_graph = false;   // caller is capturing
   }
-  if (!use_graph) return run_ops(x, s, prof);
+  if (prof && use_graph && g_cfg.profile.load() == 1) {
+    // One-off replay of the same schedule with an event-record node around
+    // every kernel group, so that the per-kind times are the graph's device
+    // times, without the host's launch gaps.
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    const uint64_t before = g_kernel_launches.load();
+    rc = run_ops(x, s, true);
+    const uint64_t kernels = g_kernel_launches.load() - before;
+    g_kernel_launches.fetch_sub(kernels);
+    cudaGraph_t graph = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(s, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (ee != cudaSuccess) return cuda_fail(ee);
+    cudaGraphExec_t exec = nullptr;
+    ee = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ee != cudaSuccess) return cuda_fail(ee);
+    ee = cudaGraphLaunch(exec, s);
+    cudaGraphExecDestroy(exec);             // the launched replay still completes
+    if (ee != cudaSuccess) return cuda_fail(ee);
+    g_kernel_launches.fetch_add(kernels);
+    return POLAR_OK;
+  }
+  if (prof || !use_graph) return run_ops(x, s, prof);
 
   GraphKey key{fs->id, g.nframes, g.llr, g.fv, g.xhat, g.uhat, g.fkind, g.prec, t,
                (shortcuts ? 1 : 0) | (opt.fuse ? 2 : 0), s, dev, ws};
@@ -617,7 +643,8 @@ int polar_config_set(const char *key, long value) {
   } else if (!strcmp(key, "plain")) {
     g_cfg.plain = value ? 1 : 0;
   } else if (!strcmp(key, "profile")) {
-    g_cfg.profile = value ? 1 : 0;
+    if (value < 0 || value > 2) return POLAR_EINVAL;
+    g_cfg.profile = value;
   } else if (!strcmp(key, "fuse")) {
     g_cfg.fuse = value ? 1 : 0;
   } else if (!strcmp(key, "autotune")) {
@@ -750,7 +777,7 @@ int polar_llr_from_channel(polar_channel ch, double param, const void *y_dev, in
 
 int polar_encode(uint32_t log2n, int nframes, const uint32_t *in_dev, uint32_t *out_dev,
                  void *stream) {
-  if (log2n < 1 || log2n > 26 || nframes < 1 || !in_dev || !out_dev) return POLAR_EINVAL;
+  if (log2n < 1 || log2n > 27 || nframes < 1 || !in_dev || !out_dev) return POLAR_EINVAL;
   if (!aligned(in_dev, 4) || !aligned(out_dev, 4)) return POLAR_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t W = log2n >= 5 ? (size_t(1) << (log2n - 5)) : 1;

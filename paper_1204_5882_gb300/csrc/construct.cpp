@@ -3,7 +3,7 @@
 // reliabilities freeze the lower index first).
 //
 // Reliability measures, in double precision and in the log domain so that
-// nothing underflows up to N = 2^26:
+// nothing underflows up to N = 2^27:
 //   BSC     Bhattacharyya recursion  ln Z- = ln Z + ln(2 - Z),  ln Z+ = 2 ln Z,
 //           ln Z0 = ln 2 + (ln p + ln(1 - p)) / 2;
 //   BIAWGN  Gaussian approximation of density evolution (Chung, Richardson,
@@ -143,7 +143,7 @@ static polar_frozen_set *new_set(uint32_t log2n) {
 
 int build_frozen_set(uint32_t log2n, polar_channel ch, double param, double rate,
                      polar_frozen_set **out) {
-  if (!out || log2n < 1 || log2n > 26) return POLAR_EINVAL;
+  if (!out || log2n < 1 || log2n > 27) return POLAR_EINVAL;
   if (!(rate >= 0.0 && rate <= 1.0)) return POLAR_EINVAL;
   if (ch == POLAR_BSC) {
     if (!(param > 0.0 && param < 0.5)) return POLAR_EINVAL;
@@ -405,7 +405,7 @@ int tv_bit_channel_pe(uint32_t log2n, polar_channel ch, double param, int mu,
 
 int build_frozen_set_tv(uint32_t log2n, polar_channel ch, double param, int mu, double rate,
                         double sum_pe_max, polar_frozen_set **out) {
-  if (!out || log2n < 1 || log2n > 26 || mu < 2 || mu > 128 || (mu & 1)) return POLAR_EINVAL;
+  if (!out || log2n < 1 || log2n > 27 || mu < 2 || mu > 128 || (mu & 1)) return POLAR_EINVAL;
   if (!(rate >= 0.0 && rate <= 1.0) || !(sum_pe_max >= 0.0)) return POLAR_EINVAL;
   if (ch == POLAR_BSC) {
     if (!(param > 0.0 && param < 0.5)) return POLAR_EINVAL;
@@ -450,7 +450,7 @@ int build_frozen_set_tv(uint32_t log2n, polar_channel ch, double param, int mu, 
 }
 
 int frozen_set_from_mask(uint32_t log2n, const uint32_t *mask, polar_frozen_set **out) {
-  if (!out || !mask || log2n < 1 || log2n > 26) return POLAR_EINVAL;
+  if (!out || !mask || log2n < 1 || log2n > 27) return POLAR_EINVAL;
   polar_frozen_set *fs = new_set(log2n);
   if (!fs) return POLAR_ENOMEM;
   const uint64_t W = fs->mask.size();

@@ -436,7 +436,7 @@ int polar_server_create(const polar_server_config *cfg, polar_server **out) {
   if (cfg->max_inflight < 1 || cfg->max_inflight > (cfg->persistent ? 4096 : 256) ||
       cfg->max_queue < 1)
     return POLAR_EINVAL;
-  if (cfg->persistent && (cfg->prec != POLAR_FP32 || cfg->max_log2n < 0 || cfg->max_log2n > 26))
+  if (cfg->persistent && (cfg->prec != POLAR_FP32 || cfg->max_log2n < 0 || cfg->max_log2n > 27))
     return POLAR_EINVAL;
   if (cfg->fkind != POLAR_F_MINSUM && cfg->fkind != POLAR_F_EXACT) return POLAR_EINVAL;
   if (cfg->prec != POLAR_FP32 && cfg->prec != POLAR_FP16 && cfg->prec != POLAR_INT8)

@@ -80,7 +80,7 @@ def test_argument_errors_are_host_side(P):
     assert L.polar_llr_from_channel(1, -1.0, 16, 0, 16, 64, None) == P.POLAR_EINVAL
     assert L.polar_llr_from_channel(1, 1.0, 16, 0, 16, 0, None) == P.POLAR_OK   # empty
     assert L.polar_encode(0, 1, 16, 16, None) == P.POLAR_EINVAL
-    assert L.polar_encode(27, 1, 16, 16, None) == P.POLAR_EINVAL
+    assert L.polar_encode(28, 1, 16, 16, None) == P.POLAR_EINVAL
     # persistent decoder: empty queue, null table, non-float32 storage
     desc = (P.FrameDesc * 1)(P.FrameDesc(fs.handle.value, 16, 16, 16, None))
     assert L.polar_sc_decode_persistent(0, desc, 0, 0, None) == P.POLAR_EINVAL
@@ -145,7 +145,7 @@ def test_server_config_rejected_on_host(P):
                 P.ServerConfig(0, 4, 16, 1 << 30, 0, 0, 99),
                 P.ServerConfig(-1, 4, 16, 1 << 30, 0, 0, 0),
                 P.ServerConfig(0, 4, 16, 1 << 30, 0, 1, 0, 1, 0),      # persistent needs fp32
-                P.ServerConfig(0, 4, 16, 1 << 30, 0, 0, 0, 1, 27),     # max_log2n range
+                P.ServerConfig(0, 4, 16, 1 << 30, 0, 0, 0, 1, 28),     # max_log2n range
                 P.ServerConfig(0, 5000, 16, 1 << 30, 0, 0, 0, 1, 0),   # resident CTA cap
                 P.ServerConfig(0, 4, 16, 1 << 30, 0, 0, 0, 2, 0)):
         assert P.lib().polar_server_create(C.byref(cfg), C.byref(h)) == P.POLAR_EINVAL

@@ -319,3 +319,28 @@ def test_autotune_picks_a_schedule_and_keeps_results(P):
         assert np.array_equal(S.unpack_bits(got[f], w.N), ox)
     assert torch.equal(xh, xh2)
     P.polar_tune_clear()
+
+
+def test_table1_largest_code_2_27_sampled(P):
+    """Table 1's longest code: N = 2^27 on the BI-AWGN channel at SNR 0.161
+    (sigma^2 = 1 / 0.161), rate 0.10 (GA set).  Two frames decoded together,
+    the first compared element by element with the float32 min-sum oracle."""
+    n, s2, R = 27, 1.0 / 0.161, 0.10
+    N = 1 << n
+    fs = P.polar_build_frozen_set(n, "biawgn", s2, R)
+    ofz, K = O.frozen_set(n, "biawgn", s2, R)
+    assert fs.K == K and np.array_equal(S.unpack_bits(fs.mask(), N), ofz)
+    xs, ys = zip(*[S.device_frame("biawgn", s2, N, 0x7AB1E + 27, i, DEV) for i in range(2)])
+    x, y = torch.stack(xs), torch.stack(ys)
+    del xs, ys
+    fv = torch.empty_like(x)
+    P.polar_reveal(fs, 2, x, fv)
+    llr = torch.empty(2, N, dtype=torch.float32, device=DEV)
+    P.polar_llr_from_channel("biawgn", s2, y, llr)
+    xh = torch.full_like(x, -1)
+    P.polar_sc_decode_many(fs, 2, llr, fv, xh, None, "minsum", "fp32")
+    torch.cuda.synchronize()
+    L0 = llr[0].cpu().numpy()
+    fvb = S.unpack_bits(words_np(fv[0]), N)
+    _, ox = O.sc_decode(L0, ofz, fvb, "minsum")
+    assert np.array_equal(S.unpack_bits(words_np(xh[0]), N), ox)

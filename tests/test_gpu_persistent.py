@@ -31,7 +31,7 @@ def P():
 
 @pytest.fixture(autouse=True)
 def default_config(P):
-    saved = {k: P.polar_config_get(k) for k in ("persist_log2", "persistent")}
+    saved = {k: P.polar_config_get(k) for k in ("persist_log2", "persistent", "subtree_log2")}
     yield
     for k, v in saved.items():
         P.polar_config_set(k, v)
@@ -201,6 +201,7 @@ def test_decode_batch_takes_the_persistent_launch(P):
     assert P.polar_kernel_launches() - before == 1
     check_against_oracle(frames, inputs)
     P.polar_config_set("persistent", 0)
+    P.polar_config_set("subtree_log2", 9)           # several launches per frame
     for f in frames:
         f[3].fill_(-1)
     before = P.polar_kernel_launches()
