@@ -73,6 +73,10 @@ def parse():
     ap.add_argument("--table1-oracle-frames", type=int, default=256)
     ap.add_argument("--table1-max-log2n", type=int, default=27)
     ap.add_argument("--tv-mu", type=int, default=16)
+    ap.add_argument("--figures", action="store_true",
+                    help="efficiency curves of Figs. 1 and 2 from the degraded construction "
+                         "(host only)")
+    ap.add_argument("--fig-max-log2n", type=int, default=27)
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip polar_autotune (subtree size / fused steps) before timing")
     ap.add_argument("--subtree-log2", type=int, default=None,
@@ -140,6 +144,30 @@ def oracle_rate(times, cores, N):
     """Aggregate rate of `cores` independent workers at the measured per-frame
     speed, in Mbit/s."""
     return cores * N / statistics.mean(times) / 1e6
+
+
+# ------------------------------------------------------------------ ranks
+# Frames are independent, so N ranks are replicas: rank r decodes its own
+# frames [r F, (r + 1) F) of the workload's seeded stream, with no collective
+# on the data path; only the timing is combined (maximum over ranks).
+def rank_first_frame(rank: int, frames_per_rank: int) -> int:
+    return rank * frames_per_rank
+
+
+def max_over_ranks(value: float, dist, device) -> float:
+    """Largest value over all ranks of the default process group (NCCL on
+    GPUs, gloo in the CPU tests); the value itself with a single rank."""
+    import torch
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, frames_per_rank: int, N: int, ms: float) -> float:
+    """Whole-job decoded Mbit/s: every rank's bits over the slowest rank's time."""
+    return world * frames_per_rank * N / (ms / 1e3) / 1e6
 
 
 def run_reference(args):
@@ -306,7 +334,7 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     w = S.WORKLOADS[args.workload]
     F, N = w.frames, w.N
-    first = rank * F
+    first = rank_first_frame(rank, F)
 
     # CPU baseline pool first (spawned, before heavy GPU work).
     pool = cores = None
@@ -365,15 +393,12 @@ def run_ours(args):
         launches = P.polar_kernel_launches() - launches0
         ck = clocks.stop()
         step_ms = [a.elapsed_time(b) for a, b in ev]
-        total_ms = sum(step_ms)
+        total_ms = max_over_ranks(sum(step_ms), dist, dev)
         if world > 1:
-            t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
             dist.barrier()
         torch.cuda.synchronize(dev)
         ms_step = total_ms / args.steps
-        value = world * F * N / (ms_step / 1e3) / 1e6
+        value = job_rate(world, F, N, ms_step)
 
         # ---- end to end through the public API with pinned host buffers
         if w.channel == "bsc":
@@ -403,22 +428,19 @@ def run_ours(args):
         stream.synchronize()
         e2e_ms = [a.elapsed_time(b) for a, b in e2e_ev]
         assert torch.equal(xh_host, xh.cpu()), "end-to-end output differs from the resident run"
-        e2e_ms_mean = sum(e2e_ms) / len(e2e_ms)
-        if world > 1:
-            t = torch.tensor([e2e_ms_mean], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms_mean = float(t.item())
-        e2e = {"value": world * F * N / (e2e_ms_mean / 1e3) / 1e6, "unit": UNIT,
+        e2e_ms_mean = max_over_ranks(sum(e2e_ms) / len(e2e_ms), dist, dev)
+        e2e = {"value": job_rate(world, F, N, e2e_ms_mean), "unit": UNIT,
                "h2d_bytes_per_step": int(y_host.numel() * y_host.element_size()
                                          + fv_host.numel() * fv_host.element_size()),
                "d2h_bytes_per_step": int(xh_host.numel() * xh_host.element_size()),
                "ms_per_step": e2e_ms_mean}
 
-        # ---- per-kernel timing pass: the step's schedule replayed once as a
-        # graph with CUDA event nodes around every kernel group (profile = 1);
-        # eager launches with events (profile = 2) if that records nothing
-        prof_mode = "graph replay with event nodes"
-        for mode in (1, 2):
+        # ---- per-kernel timing pass: eager launches with CUDA events around
+        # every kernel group (profile = 2; event nodes inside a graph replay,
+        # profile = 1, perturb the short kernels more), the graph form if the
+        # eager pass records nothing
+        prof_mode = "eager launches with events"
+        for mode in (2, 1):
             P.polar_config_set("profile", mode)
             P.polar_profile_reset()
             flush.zero_()
@@ -428,7 +450,7 @@ def run_ours(args):
             P.polar_config_set("profile", 0)
             if sum(v[1] for v in prof.values()) > 1:
                 break
-            prof_mode = "eager launches with events"
+            prof_mode = "graph replay with event nodes"
 
         # ---- plain per-frame baseline on a few frames
         plain = None
@@ -700,8 +722,15 @@ def run_table1(args):
             continue
         N = 1 << n
         t0 = time.perf_counter()
-        mu = args.tv_mu if n <= 24 else min(args.tv_mu, 8)       # 2^27: about a minute
-        fs = P.polar_build_frozen_set_tv(n, ch, par, mu, 0.0, 0.1)
+        # BSC: degraded-channel bounds; BI-AWGN: Gaussian approximation (its
+        # estimates track the paper's density evolution, where the mu = 16
+        # degraded bound is loose at low SNR)
+        if ch == "bsc":
+            fs = P.polar_build_frozen_set_tv(n, ch, par, args.tv_mu, 0.0, 0.1)
+            how = f"degraded (Tal-Vardy), mu = {args.tv_mu}, sum P_e <= 0.1"
+        else:
+            fs = P.polar_build_frozen_set_sum(n, ch, par, 0.1)
+            how = "Gaussian approximation, sum P_e <= 0.1"
         build_s = time.perf_counter() - t0
         C = capacity_of(ch, par)
         frames = args.table1_frames if n <= 16 else (args.table1_frames // 4 if n <= 20
@@ -745,7 +774,7 @@ def run_table1(args):
             done += b
         row = {"channel": ch, "param": par, "N": N, "K": fs.K, "rate": fs.K / N,
                "beta": fs.K / N / C, "capacity": C, "sum_pe_bound": fs.sum_pe,
-               "construction": f"degraded (Tal-Vardy), mu = {mu}, sum P_e <= 0.1",
+               "construction": how,
                "construction_s": build_s, "frames": frames,
                "fer_minsum": _wilson(err["minsum"], frames),
                "fer_exact": _wilson(err["exact"], frames),
@@ -764,6 +793,42 @@ def run_table1(args):
         print(json.dumps({"table1_row": row}), flush=True)
     print(json.dumps({"metric": "Table 1 reproduction: efficiency, FER and decoded Mbit/s",
                       "data": "synthetic", "rows": rows}), flush=True)
+
+
+# ------------------------------------------------------------------ Figs. 1 and 2
+def run_figures(args):
+    """Efficiency beta = R / C at Sec. 3's FER budget (sum P_e <= 0.1):
+    Fig. 1 (BSC, p = 1..11 %, N = 2^16..2^24; degraded-channel bounds) and
+    Fig. 2 (BI-AWGN at the SNRs 1.097, 0.161, 0.075, 0.029, N = 2^17..2^27
+    odd; Gaussian approximation, with the degraded bound up to 2^23).  Host
+    construction only (all host cores)."""
+    from paper_1204_5882_gb300 import polar as P
+
+    out = {"fig1_bsc": [], "fig2_biawgn": []}
+    for n in range(16, min(args.fig_max_log2n, 24) + 1, 2):
+        for pp in [k / 100 for k in range(1, 12)]:
+            mu = args.tv_mu if n <= 22 else min(args.tv_mu, 16)
+            t0 = time.perf_counter()
+            fs = P.polar_build_frozen_set_tv(n, "bsc", pp, mu, 0.0, 0.1)
+            row = {"log2n": n, "p": pp, "K": fs.K, "beta": fs.K / fs.N / capacity_of("bsc", pp),
+                   "sum_pe": fs.sum_pe, "mu": mu, "seconds": time.perf_counter() - t0}
+            out["fig1_bsc"].append(row)
+            print(json.dumps({"fig1": row}), flush=True)
+    for n in range(17, min(args.fig_max_log2n, 27) + 1, 2):
+        for snr in (1.097, 0.161, 0.075, 0.029):
+            C = capacity_of("biawgn", 1.0 / snr)
+            t0 = time.perf_counter()
+            fs = P.polar_build_frozen_set_sum(n, "biawgn", 1.0 / snr, 0.1)
+            row = {"log2n": n, "snr": snr, "K": fs.K, "beta": fs.K / fs.N / C,
+                   "construction": "Gaussian approximation", "sum_pe": fs.sum_pe,
+                   "seconds": time.perf_counter() - t0}
+            if n <= 23:                        # the degraded bound beside it
+                tv = P.polar_build_frozen_set_tv(n, "biawgn", 1.0 / snr, args.tv_mu, 0.0, 0.1)
+                row["beta_degraded_bound"] = tv.K / tv.N / C
+            out["fig2_biawgn"].append(row)
+            print(json.dumps({"fig2": row}), flush=True)
+    print(json.dumps({"metric": "efficiency at sum P_e <= 0.1 (Figs. 1 and 2)",
+                      "construction": "degraded (Tal-Vardy)", "rows": out}), flush=True)
 
 
 # ------------------------------------------------------------------ precision sweep
@@ -881,6 +946,8 @@ def main():
         run_precision_sweep(args)
     elif args.table1:
         run_table1(args)
+    elif args.figures:
+        run_figures(args)
     else:
         run_ours(args)
 

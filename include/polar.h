@@ -92,6 +92,12 @@ const char *polar_last_error_string(void);
  *   "int8_target"   INT8 storage: the per-frame scale is the power of two
  *                   2^rint(log2(target / mean|L|)) (mean in double over the
  *                   frame's channel LLRs); 1..64, default 8.
+ *   "pdl"           1 = launch the kernels of a decode with programmatic
+ *                   dependent launch: each waits for its predecessor's
+ *                   completion on the device while its own launch overlaps
+ *                   the predecessor's tail; 0 (default) = plain stream order
+ *                   (graph replays already keep the gaps short; PDL measured
+ *                   no faster).  Results do not depend on it.
  *   "persistent"    how polar_sc_decode_batch runs float32 batches: 0 =
  *                   always as launched groups of equally strided frames;
  *                   1 (default) = in one persistent launch
@@ -134,6 +140,15 @@ void polar_profile_reset(void);
  * sigma^2 <= 0, rate outside [0, 1], out == NULL. */
 int polar_build_frozen_set(uint32_t log2n, polar_channel ch, double param,
                            double rate, polar_frozen_set **out);
+
+/* As polar_build_frozen_set, with K chosen by Sec. 3's rule instead of a
+ * rate: the largest K whose most reliable bit-channels have sum_i P_e,i <=
+ * sum_pe_max, with P_e,i = Z_i (BSC: the Bhattacharyya parameter, an upper
+ * bound on the error probability, loose at high rates) or the Gaussian-
+ * approximation estimate Q(sqrt(m_i / 2)) (BI-AWGN: an estimate, not a
+ * bound).  EINVAL as polar_build_frozen_set, or sum_pe_max < 0. */
+int polar_build_frozen_set_sum(uint32_t log2n, polar_channel ch, double param,
+                               double sum_pe_max, polar_frozen_set **out);
 
 /* Frozen set from the degraded-channel construction (Sec. 3's density
  * evolution made finite, after Tal & Vardy 2013): every bit-channel is

@@ -71,6 +71,8 @@ def lib():
         L.or_tv_pe.restype = C.c_int
         L.or_k_for_sum.argtypes = [C.c_int, P, C.c_double]
         L.or_k_for_sum.restype = C.c_uint64
+        L.or_k_for_sum_log.argtypes = [C.c_int, P, C.c_double]
+        L.or_k_for_sum_log.restype = C.c_uint64
         L.or_capacity_bsc.argtypes = [C.c_double]
         L.or_capacity_bsc.restype = C.c_double
         L.or_capacity_biawgn.argtypes = [C.c_double]
@@ -239,6 +241,21 @@ def k_for_sum(bad, target: float) -> int:
     """Largest K whose K most reliable entries of `bad` sum to <= target."""
     bad = np.ascontiguousarray(np.asarray(bad, dtype=np.float64))
     return int(lib().or_k_for_sum(log2_of(bad.size), _p(bad), float(target)))
+
+
+def k_for_sum_log(lbad, target: float) -> int:
+    """k_for_sum on log-domain reliabilities (order by the logs, sum exp)."""
+    lbad = np.ascontiguousarray(np.asarray(lbad, dtype=np.float64))
+    return int(lib().or_k_for_sum_log(log2_of(lbad.size), _p(lbad), float(target)))
+
+
+def frozen_set_sum(n: int, channel: str, param: float, sum_pe_max: float = 0.1):
+    """(frozen mask, K, sum) of the Bhattacharyya (BSC) / GA (BI-AWGN) set
+    whose K is chosen by Sec. 3's rule on those reliabilities."""
+    lb = unreliability(n, channel, param)
+    K = k_for_sum_log(lb, sum_pe_max)
+    fz = select_frozen(lb, K)
+    return fz, K, float(np.exp(lb[fz == 0]).sum())
 
 
 def frozen_set_tv(n: int, channel: str, param: float, rate: float = 0.0,

@@ -625,6 +625,26 @@ OR_API uint64_t or_k_for_sum(int n, const double *bad, double target)
     return K;
 }
 
+/* The same rule on log-domain reliabilities (ln Z or ln P_e): the order is   */
+/* that of the logs, the sum is of their exponentials.                      */
+OR_API uint64_t or_k_for_sum_log(int n, const double *lbad, double target)
+{
+    size_t N = (size_t)1 << n;
+    uint32_t *idx = (uint32_t *)malloc(sizeof(uint32_t) * N);
+    for (size_t i = 0; i < N; i++) idx[i] = (uint32_t)i;
+    g_bad = lbad;
+    qsort(idx, N, sizeof(uint32_t), cmp_unrel);
+    double acc = 0.0;
+    uint64_t K = 0;
+    for (size_t r = N; r-- > 0;) {
+        acc += exp(lbad[idx[r]]);
+        if (acc > target) break;
+        K++;
+    }
+    free(idx);
+    return K;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Capacities for the efficiency beta = R / C (Sec. 2.1, Eq. 3).            */
 /* BSC: C = 1 - h2(p).  BIAWGN with x = 0 sent (+1):                        */

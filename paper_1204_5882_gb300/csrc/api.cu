@@ -69,17 +69,25 @@ struct ProfScope {
   double bytes;
   cudaStream_t s;
   cudaEvent_t a = nullptr, b = nullptr;
+  bool captured = false;   // inside a stream capture: record as event nodes of the graph
   ProfScope(bool enable, int k, double by, cudaStream_t st) : on(enable), kind(k), bytes(by), s(st) {
     if (!on) return;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+      cudaGetLastError();
       on = false;
       return;
     }
-    cudaEventRecord(a, s);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    captured = cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+    record(a);
+  }
+  void record(cudaEvent_t e) {
+    if (captured) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    else cudaEventRecord(e, s);
   }
   ~ProfScope() {
     if (!on) return;
-    cudaEventRecord(b, s);
+    record(b);
     std::lock_guard<std::mutex> g(g_prof_mu);
     g_prof_pending.push_back({kind, a, b, bytes});
   }
@@ -93,6 +101,8 @@ void prof_drain() {
       g_prof_ms[r.kind] += ms;
       g_prof_n[r.kind] += 1;
       g_prof_bytes[r.kind] += r.bytes;
+    } else {
+      cudaGetLastError();                 // not the caller's error to see later
     }
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -102,6 +112,7 @@ void prof_drain() {
 
 int cuda_fail(cudaError_t e) {
   g_last_error = cudaGetErrorString(e);
+  cudaGetLastError();                     // reported here; leave no stale error behind
   return POLAR_ECUDA;
 }
 
@@ -329,6 +340,7 @@ Opts opts_for(const polar_frozen_set *fs, int nframes, int fkind, int prec) {
 }
 
 int decode_group(const Group &g, cudaStream_t s, const Opts &opt) {
+  NvtxRange nv("polar decode batch");
   polar_frozen_set *fs = g.fs;
   const int n = (int)fs->log2n;
   const bool plain = opt.plain;
@@ -407,7 +419,7 @@ int decode_group(const Group &g, cudaStream_t s, const Opts &opt) {
   if (prof || !use_graph) return run_ops(x, s, prof);
 
   GraphKey key{fs->id, g.nframes, g.llr, g.fv, g.xhat, g.uhat, g.fkind, g.prec, t,
-               (shortcuts ? 1 : 0) | (opt.fuse ? 2 : 0), s, dev, ws};
+               (shortcuts ? 1 : 0) | (opt.fuse ? 2 : 0) | (g_pdl.load() ? 4 : 0), s, dev, ws};
   cudaGraphExec_t exec = nullptr;
   uint64_t kernels = 0;
   {
@@ -474,6 +486,7 @@ int check_frames(int nframes, const polar_frame_desc *frames, int fkind, int pre
 // ones fill in behind them.
 int decode_persistent(int nframes, const polar_frame_desc *frames, int fkind, int prec,
                       cudaStream_t s) {
+  NvtxRange nv("polar decode persistent");
   if (prec != POLAR_FP32) {
     g_last_error = "the persistent decoder keeps float32 levels";
     return POLAR_EINVAL;
@@ -652,6 +665,8 @@ int polar_config_set(const char *key, long value) {
   } else if (!strcmp(key, "int8_target")) {
     if (value < 1 || value > 64) return POLAR_EINVAL;
     g_cfg.int8_target = value;
+  } else if (!strcmp(key, "pdl")) {
+    g_pdl = value ? 1 : 0;
   } else if (!strcmp(key, "persist_log2")) {
     if (value < 5 || value > 14) return POLAR_EINVAL;
     g_cfg.persist_log2 = value;
@@ -676,6 +691,7 @@ int polar_config_get(const char *key, long *value) {
   else if (!strcmp(key, "autotune")) *value = g_cfg.autotune;
   else if (!strcmp(key, "persistent")) *value = g_cfg.persistent;
   else if (!strcmp(key, "persist_log2")) *value = g_cfg.persist_log2;
+  else if (!strcmp(key, "pdl")) *value = g_pdl.load();
   else return POLAR_ENOTFOUND;
   return POLAR_OK;
 }
@@ -711,6 +727,11 @@ void polar_profile_reset(void) {
 int polar_build_frozen_set(uint32_t log2n, polar_channel ch, double param, double rate,
                            polar_frozen_set **out) {
   return build_frozen_set(log2n, ch, param, rate, out);
+}
+
+int polar_build_frozen_set_sum(uint32_t log2n, polar_channel ch, double param,
+                               double sum_pe_max, polar_frozen_set **out) {
+  return build_frozen_set_sum(log2n, ch, param, sum_pe_max, out);
 }
 
 int polar_build_frozen_set_tv(uint32_t log2n, polar_channel ch, double param, int mu,
@@ -826,6 +847,7 @@ int polar_sc_decode(const polar_frozen_set *fs, const float *llr_dev,
 int polar_autotune(const polar_frozen_set *fs_c, int nframes, const float *llr_dev,
                    const uint32_t *frozen_vals_dev, uint32_t *xhat_dev, polar_fkind fkind,
                    polar_prec prec, void *stream, int *best_t, int *best_fuse, double *best_ms) {
+  NvtxRange nv("polar autotune");
   Group g{const_cast<polar_frozen_set *>(fs_c), nframes, llr_dev, frozen_vals_dev, xhat_dev,
           nullptr, (int)fkind, (int)prec};
   int rc = check_group(g);

@@ -141,10 +141,13 @@ static polar_frozen_set *new_set(uint32_t log2n) {
   return fs;
 }
 
-int build_frozen_set(uint32_t log2n, polar_channel ch, double param, double rate,
-                     polar_frozen_set **out) {
+// Bhattacharyya (BSC) / GA (BI-AWGN) set; K = floor(rate N), or (sum_rule)
+// the largest K whose most reliable channels have sum exp(bad) <= sum_max.
+static int bound_set(uint32_t log2n, polar_channel ch, double param, bool sum_rule,
+                     double rate, double sum_max, polar_frozen_set **out) {
+  NvtxRange nv("polar construct (bound / GA)");
   if (!out || log2n < 1 || log2n > 27) return POLAR_EINVAL;
-  if (!(rate >= 0.0 && rate <= 1.0)) return POLAR_EINVAL;
+  if (!(rate >= 0.0 && rate <= 1.0) || !(sum_max >= 0.0)) return POLAR_EINVAL;
   if (ch == POLAR_BSC) {
     if (!(param > 0.0 && param < 0.5)) return POLAR_EINVAL;
   } else if (ch == POLAR_BIAWGN) {
@@ -169,8 +172,6 @@ int build_frozen_set(uint32_t log2n, polar_channel ch, double param, double rate
   }
   polar_frozen_set *fs = new_set(log2n);
   if (!fs) return POLAR_ENOMEM;
-  fs->K = (uint64_t)std::floor(rate * (double)N);
-  if (fs->K > N) fs->K = N;
   // Rank by unreliability (descending), lower index first on ties; the
   // first N-K are frozen.
   std::vector<uint32_t> idx(N);
@@ -179,14 +180,37 @@ int build_frozen_set(uint32_t log2n, polar_channel ch, double param, double rate
     if (bad[a] != bad[b]) return bad[a] > bad[b];
     return a < b;
   };
+  if (sum_rule) {
+    std::sort(idx.begin(), idx.end(), worse);
+    double acc = 0.0;
+    fs->K = 0;
+    for (uint64_t r = N; r-- > 0;) {
+      acc += std::exp(bad[idx[r]]);
+      if (acc > sum_max) break;
+      ++fs->K;
+    }
+  } else {
+    fs->K = std::min<uint64_t>(N, (uint64_t)std::floor(rate * (double)N));
+  }
   const uint64_t nf = N - fs->K;
-  if (nf > 0 && nf < N) std::nth_element(idx.begin(), idx.begin() + nf, idx.end(), worse);
+  if (!sum_rule && nf > 0 && nf < N)
+    std::nth_element(idx.begin(), idx.begin() + nf, idx.end(), worse);
   for (uint64_t r = 0; r < nf; ++r) fs->mask[idx[r] >> 5] |= 1u << (idx[r] & 31);
   double s = 0.0;
   for (uint64_t r = nf; r < N; ++r) s += std::exp(bad[idx[r]]);
   fs->sum_pe = s;
   *out = fs;
   return POLAR_OK;
+}
+
+int build_frozen_set(uint32_t log2n, polar_channel ch, double param, double rate,
+                     polar_frozen_set **out) {
+  return bound_set(log2n, ch, param, false, rate, 0.0, out);
+}
+
+int build_frozen_set_sum(uint32_t log2n, polar_channel ch, double param, double sum_pe_max,
+                         polar_frozen_set **out) {
+  return bound_set(log2n, ch, param, true, 0.0, sum_pe_max, out);
 }
 
 // ---------------------------------------------------------------- degraded construction
@@ -405,6 +429,7 @@ int tv_bit_channel_pe(uint32_t log2n, polar_channel ch, double param, int mu,
 
 int build_frozen_set_tv(uint32_t log2n, polar_channel ch, double param, int mu, double rate,
                         double sum_pe_max, polar_frozen_set **out) {
+  NvtxRange nv("polar construct (degraded)");
   if (!out || log2n < 1 || log2n > 27 || mu < 2 || mu > 128 || (mu & 1)) return POLAR_EINVAL;
   if (!(rate >= 0.0 && rate <= 1.0) || !(sum_pe_max >= 0.0)) return POLAR_EINVAL;
   if (ch == POLAR_BSC) {

@@ -2,9 +2,44 @@
 #pragma once
 
 #include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <atomic>
 #include <cstdint>
+#include <utility>
 
 namespace polar {
+
+// ---------------------------------------------------------------- launches
+// Programmatic dependent launch (PDL): a kernel of the decode sequence first
+// waits until the grids it depends on have completed and their writes are
+// visible, then lets the next grid of the stream start launching, so that
+// the next kernel's launch and block scheduling overlap this one's tail.
+// Both instructions are no-ops in a grid launched without the attribute.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+extern std::atomic<int> g_pdl;   // 1 = launch the decode sequence with PDL
+
+// <<<grid, block, smem, s>>> with the programmatic-serialization attribute
+// when g_pdl is set.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                     cudaStream_t s, Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = g_pdl.load(std::memory_order_relaxed);
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 // ---------------------------------------------------------------- f and g
 // Min-sum check-node update: sign = - iff exactly one input has its sign bit

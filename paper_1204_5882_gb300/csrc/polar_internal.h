@@ -14,6 +14,8 @@
 
 #include "polar.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 // Small index helpers used by host and device code.
 #ifdef __CUDACC__
 #define POLAR_HD __host__ __device__
@@ -74,6 +76,8 @@ namespace polar {
 // --- construction (construct.cpp) -----------------------------------------
 int build_frozen_set(uint32_t log2n, polar_channel ch, double param, double rate,
                      polar_frozen_set **out);
+int build_frozen_set_sum(uint32_t log2n, polar_channel ch, double param, double sum_pe_max,
+                         polar_frozen_set **out);
 int frozen_set_from_mask(uint32_t log2n, const uint32_t *mask, polar_frozen_set **out);
 // Degraded-channel (Tal-Vardy) construction: bit-channel error bounds, and
 // the frozen set they give (K = floor(rate N), or by the sum rule if rate = 0).
@@ -216,8 +220,18 @@ int decode_eager(const polar_frozen_set *fs, int nframes, const float *llr, cons
 size_t decode_scratch_bytes(const polar_frozen_set *fs, int nframes, int prec);
 void release_stream_workspace(int dev, cudaStream_t s);
 
+// NVTX range over a host-side stage (a no-op unless a profiler is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 // Kernels launched by this library (graph replays included).
 extern std::atomic<uint64_t> g_kernel_launches;
+// 1 = decode kernels are launched with programmatic dependent launch.
+extern std::atomic<int> g_pdl;
 inline cudaError_t counted(cudaError_t e, uint64_t kernels) {
   if (e == cudaSuccess) g_kernel_launches.fetch_add(kernels, std::memory_order_relaxed);
   return e;

@@ -225,6 +225,8 @@ void ring_collect(polar_server *s) {
 
 // Publishes the oldest pending requests while the ring has room.
 void ring_publish(polar_server *s) {
+  if (s->queue.empty()) return;
+  polar::NvtxRange nv("polar server publish");
   Ring &r = s->pr;
   int dev = s->cfg.device;
   while (!s->queue.empty()) {

@@ -17,6 +17,7 @@ static inline int grid_for(size_t work, int block, int max_blocks = 152 * 16) {
 // BSC (Sec. 1): L = y ? -c : c; one float4 per thread (4 bits of y).
 __global__ void k_llr_bsc(const uint32_t *__restrict__ y, float4 *__restrict__ llr,
                           size_t n4, float c) {
+  pdl_enter();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4;
        i += (size_t)gridDim.x * blockDim.x) {
     uint32_t b = (y[i >> 3] >> ((i & 7) * 4)) & 0xFu;
@@ -32,6 +33,7 @@ __global__ void k_llr_bsc(const uint32_t *__restrict__ y, float4 *__restrict__ l
 // BI-AWGN (Sec. 2.2): L = float(y * (2 / sigma^2)), product in double.
 __global__ void k_llr_biawgn(const double2 *__restrict__ y, float2 *__restrict__ llr,
                              size_t n2, double s) {
+  pdl_enter();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2;
        i += (size_t)gridDim.x * blockDim.x) {
     double2 v = y[i];
@@ -41,6 +43,7 @@ __global__ void k_llr_biawgn(const double2 *__restrict__ y, float2 *__restrict__
 
 __global__ void k_llr_biawgn_tail(const double *__restrict__ y, float *__restrict__ llr,
                                   size_t first, size_t n, double s) {
+  pdl_enter();
   size_t i = first + blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i < n) llr[i] = (float)(y[i] * s);
 }
@@ -48,25 +51,28 @@ __global__ void k_llr_biawgn_tail(const double *__restrict__ y, float *__restric
 cudaError_t launch_llr_bsc(const uint32_t *y, float *llr, size_t n_total, float c,
                            cudaStream_t s) {
   size_t n4 = n_total / 4;
-  k_llr_bsc<<<grid_for(n4, 256), 256, 0, s>>>(y, reinterpret_cast<float4 *>(llr), n4, c);
-  return counted(cudaGetLastError(), 1);
+  return counted(launch_k(k_llr_bsc, grid_for(n4, 256), 256, 0, s, y,
+                          reinterpret_cast<float4 *>(llr), n4, c), 1);
 }
 
 cudaError_t launch_llr_biawgn(const double *y, float *llr, size_t n_total, double scale,
                               cudaStream_t s) {
   size_t n2 = n_total / 2;
+  cudaError_t e = cudaSuccess;
   if (n2) {
-    k_llr_biawgn<<<grid_for(n2, 256), 256, 0, s>>>(reinterpret_cast<const double2 *>(y),
-                                                  reinterpret_cast<float2 *>(llr), n2, scale);
+    e = launch_k(k_llr_biawgn, grid_for(n2, 256), 256, 0, s, reinterpret_cast<const double2 *>(y),
+                 reinterpret_cast<float2 *>(llr), n2, scale);
   }
-  if (n_total & 1) k_llr_biawgn_tail<<<1, 32, 0, s>>>(y, llr, n2 * 2, n_total, scale);
-  return counted(cudaGetLastError(), (n2 ? 1 : 0) + (n_total & 1));
+  if (e == cudaSuccess && (n_total & 1))
+    e = launch_k(k_llr_biawgn_tail, 1, 32, 0, s, y, llr, n2 * 2, n_total, scale);
+  return counted(e, (n2 ? 1 : 0) + (n_total & 1));
 }
 
 // ---------------------------------------------------------------- transform
 // Region r of nregions covers words [base + r*stride, +nw) (nw = 2^(k-5)).
 __global__ void k_encode_inword(uint32_t *__restrict__ w, size_t stride, size_t off,
                                 size_t nw, int nregions, int k) {
+  pdl_enter();
   size_t total = nw * (size_t)nregions;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
        i += (size_t)gridDim.x * blockDim.x) {
@@ -87,6 +93,7 @@ __global__ void k_encode_inword(uint32_t *__restrict__ w, size_t stride, size_t 
 // words [r*stride + off + b*2^lv, +2^lv).
 __global__ void k_encode_xword_smem(uint32_t *__restrict__ w, size_t stride, size_t off,
                                     size_t nw, int nregions, int lv) {
+  pdl_enter();
   extern __shared__ uint32_t sm[];
   const size_t bw = size_t(1) << lv;
   const size_t blocks_per_region = nw / bw;
@@ -111,6 +118,7 @@ __global__ void k_encode_xword_smem(uint32_t *__restrict__ w, size_t stride, siz
 // One cross-word level: word a ^= word a + hw for a with bit hw clear.
 __global__ void k_encode_xword_level(uint32_t *__restrict__ w, size_t stride, size_t off,
                                      size_t nw, int nregions, size_t hw) {
+  pdl_enter();
   size_t half = nw / 2;
   size_t total = half * (size_t)nregions;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
@@ -126,31 +134,32 @@ cudaError_t launch_encode_regions(uint32_t *words, size_t stride_w, size_t off_w
                                   int nframes, cudaStream_t s) {
   size_t nw = log2len >= 5 ? (size_t(1) << (log2len - 5)) : 1;
   uint64_t launched = 1;
-  k_encode_inword<<<grid_for(nw * nframes, 256), 256, 0, s>>>(words, stride_w, off_w, nw,
-                                                              nframes, log2len);
-  if (nw > 1) {
+  cudaError_t e = launch_k(k_encode_inword, grid_for(nw * nframes, 256), 256, 0, s, words,
+                           stride_w, off_w, nw, nframes, log2len);
+  if (e == cudaSuccess && nw > 1) {
     int lvw = log2len - 5;
     int lv = lvw < 12 ? lvw : 12;
     size_t bw = size_t(1) << lv;
     size_t nblocks = (nw / bw) * nframes;
     int grid = (int)(nblocks < 4096 ? nblocks : 4096);
-    k_encode_xword_smem<<<grid, 256, bw * sizeof(uint32_t), s>>>(words, stride_w, off_w, nw,
-                                                                 nframes, lv);
+    e = launch_k(k_encode_xword_smem, grid, 256, bw * sizeof(uint32_t), s, words, stride_w,
+                 off_w, nw, nframes, lv);
     launched++;
-    for (int l = lv; l < lvw; ++l) {
+    for (int l = lv; l < lvw && e == cudaSuccess; ++l) {
       size_t hw = size_t(1) << l;
-      k_encode_xword_level<<<grid_for(nw / 2 * nframes, 256), 256, 0, s>>>(
-          words, stride_w, off_w, nw, nframes, hw);
+      e = launch_k(k_encode_xword_level, grid_for(nw / 2 * nframes, 256), 256, 0, s, words,
+                   stride_w, off_w, nw, nframes, hw);
       launched++;
     }
   }
-  return counted(cudaGetLastError(), launched);
+  return counted(e, launched);
 }
 
 // dst[f][off + j] = src[f][off + j] (& and_mask[off + j] if given).
 __global__ void k_copy_regions(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
                                size_t stride, size_t off, size_t nw, int nregions,
                                const uint32_t *__restrict__ and_mask) {
+  pdl_enter();
   size_t total = nw * (size_t)nregions;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
        i += (size_t)gridDim.x * blockDim.x) {
@@ -164,23 +173,22 @@ __global__ void k_copy_regions(const uint32_t *__restrict__ src, uint32_t *__res
 cudaError_t launch_copy_regions(const uint32_t *src, uint32_t *dst, size_t stride_w,
                                 size_t off_w, size_t nwords, int nframes,
                                 const uint32_t *and_mask, cudaStream_t s) {
-  k_copy_regions<<<grid_for(nwords * nframes, 256), 256, 0, s>>>(src, dst, stride_w, off_w,
-                                                                 nwords, nframes, and_mask);
-  return counted(cudaGetLastError(), 1);
+  return counted(launch_k(k_copy_regions, grid_for(nwords * nframes, 256), 256, 0, s, src, dst,
+                          stride_w, off_w, nwords, nframes, and_mask), 1);
 }
 
 // ---------------------------------------------------------------- combine
 // One CTA per frame; see cascade_device.
 __global__ void k_cascade(uint32_t *__restrict__ xhat, size_t stride, int ku, uint64_t ou,
                           int r) {
+  pdl_enter();
   cascade_device(xhat + blockIdx.x * stride, ku, ou, r);
 }
 
 cudaError_t launch_cascade(uint32_t *xhat, size_t stride_w, int k_unit, uint64_t o_unit, int r,
                            int nframes, cudaStream_t s) {
   if (r <= 0) return cudaSuccess;
-  k_cascade<<<nframes, 512, 0, s>>>(xhat, stride_w, k_unit, o_unit, r);
-  return counted(cudaGetLastError(), 1);
+  return counted(launch_k(k_cascade, nframes, 512, 0, s, xhat, stride_w, k_unit, o_unit, r), 1);
 }
 
 // ---------------------------------------------------------------- stream f / g
@@ -197,6 +205,7 @@ __device__ __forceinline__ float load_in(const Tin *p, float sc) {
 template <typename Tin, typename Tout, int FK>
 __global__ void k_stream_f(const Tin *__restrict__ in, size_t in_stride, Tout *__restrict__ out,
                            size_t out_stride, uint64_t h, const float *__restrict__ scale) {
+  pdl_enter();
   const Tin *a = in + blockIdx.y * in_stride;
   const Tin *b = a + h;
   Tout *o = out + blockIdx.y * out_stride;
@@ -228,6 +237,7 @@ template <typename Tin, typename Tout>
 __global__ void k_stream_g(const Tin *__restrict__ in, size_t in_stride, Tout *__restrict__ out,
                            size_t out_stride, uint64_t h, const uint32_t *__restrict__ xhat,
                            size_t x_stride, uint64_t o_bits, const float *__restrict__ scale) {
+  pdl_enter();
   const Tin *a = in + blockIdx.y * in_stride;
   const Tin *b = a + h;
   Tout *o = out + blockIdx.y * out_stride;
@@ -272,22 +282,19 @@ static cudaError_t stream_f_t(int fkind, const void *in, size_t in_stride, bool 
                               void *out, size_t out_stride, uint64_t h, int nframes,
                               const float *scale, cudaStream_t s) {
   dim3 g = stream_grid(h, nframes);
+  cudaError_t e;
   if (in_is_llr) {
-    if (fkind == 0)
-      k_stream_f<float, T, 0><<<g, 256, 0, s>>>((const float *)in, in_stride, (T *)out,
-                                                out_stride, h, scale);
-    else
-      k_stream_f<float, T, 1><<<g, 256, 0, s>>>((const float *)in, in_stride, (T *)out,
-                                                out_stride, h, scale);
+    e = fkind == 0 ? launch_k(k_stream_f<float, T, 0>, g, 256, 0, s, (const float *)in,
+                              in_stride, (T *)out, out_stride, h, scale)
+                   : launch_k(k_stream_f<float, T, 1>, g, 256, 0, s, (const float *)in,
+                              in_stride, (T *)out, out_stride, h, scale);
   } else {
-    if (fkind == 0)
-      k_stream_f<T, T, 0><<<g, 256, 0, s>>>((const T *)in, in_stride, (T *)out, out_stride, h,
-                                            scale);
-    else
-      k_stream_f<T, T, 1><<<g, 256, 0, s>>>((const T *)in, in_stride, (T *)out, out_stride, h,
-                                            scale);
+    e = fkind == 0 ? launch_k(k_stream_f<T, T, 0>, g, 256, 0, s, (const T *)in, in_stride,
+                              (T *)out, out_stride, h, scale)
+                   : launch_k(k_stream_f<T, T, 1>, g, 256, 0, s, (const T *)in, in_stride,
+                              (T *)out, out_stride, h, scale);
   }
-  return counted(cudaGetLastError(), 1);
+  return counted(e, 1);
 }
 
 template <typename T>
@@ -296,13 +303,12 @@ static cudaError_t stream_g_t(const void *in, size_t in_stride, bool in_is_llr, 
                               size_t xs, uint64_t o, int nframes, const float *scale,
                               cudaStream_t s) {
   dim3 g = stream_grid(h, nframes);
-  if (in_is_llr)
-    k_stream_g<float, T><<<g, 256, 0, s>>>((const float *)in, in_stride, (T *)out, out_stride, h,
-                                           xhat, xs, o, scale);
-  else
-    k_stream_g<T, T><<<g, 256, 0, s>>>((const T *)in, in_stride, (T *)out, out_stride, h, xhat,
-                                       xs, o, scale);
-  return counted(cudaGetLastError(), 1);
+  cudaError_t e =
+      in_is_llr ? launch_k(k_stream_g<float, T>, g, 256, 0, s, (const float *)in, in_stride,
+                           (T *)out, out_stride, h, xhat, xs, o, scale)
+                : launch_k(k_stream_g<T, T>, g, 256, 0, s, (const T *)in, in_stride, (T *)out,
+                           out_stride, h, xhat, xs, o, scale);
+  return counted(e, 1);
 }
 
 // ---------------------------------------------------------------- fused chains
@@ -382,6 +388,7 @@ __global__ void __launch_bounds__(256) k_chain(const Tin *__restrict__ in, size_
                                                const uint32_t *__restrict__ xhat,
                                                size_t x_stride, uint64_t o_left,
                                                const float *__restrict__ scale) {
+  pdl_enter();
   extern __shared__ float4 cs4[];
   const int cols = 1 << (kb - logB);
   const int f = blockIdx.x >> (kb - logB), c = blockIdx.x & (cols - 1);
@@ -455,20 +462,21 @@ static cudaError_t chain_t(const void *in, size_t in_stride, bool in_is_llr, voi
   if (logB > kb) logB = kb;
   const size_t smem = (size_t(1) << (logB + kt - kb)) * sizeof(float);
   const unsigned grid = (unsigned)nframes << (kb - logB);
+  cudaError_t e;
   if (in_is_llr) {
     auto kern = k_chain<float, T, FK, G>;
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<grid, 256, smem, s>>>((const float *)in, in_stride, (T *)lv_base, t, nframes, kt, kb,
-                                 logB, xhat, xs, o, scale);
+    e = launch_k(kern, grid, 256, smem, s, (const float *)in, in_stride, (T *)lv_base, t,
+                 nframes, kt, kb, logB, xhat, xs, o, scale);
   } else {
     auto kern = k_chain<T, T, FK, G>;
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<grid, 256, smem, s>>>((const T *)in, in_stride, (T *)lv_base, t, nframes, kt, kb,
-                                 logB, xhat, xs, o, scale);
+    e = launch_k(kern, grid, 256, smem, s, (const T *)in, in_stride, (T *)lv_base, t, nframes,
+                 kt, kb, logB, xhat, xs, o, scale);
   }
-  return counted(cudaGetLastError(), 1);
+  return counted(e, 1);
 }
 
 template <typename T>
@@ -506,6 +514,7 @@ cudaError_t launch_chain(int prec, int fkind, bool first_g, const void *in, size
 // s = 2^rint(log2(target / mean)), clamped to 2^+-100; s = 1 if every L = 0.
 __global__ void k_int8_scale(const float *__restrict__ llr, size_t n, double target,
                              float *__restrict__ scale) {
+  pdl_enter();
   __shared__ double part[256];
   const float *p = llr + blockIdx.x * n;
   double acc = 0.0;
@@ -530,11 +539,11 @@ __global__ void k_int8_scale(const float *__restrict__ llr, size_t n, double tar
 
 cudaError_t launch_int8_scale(const float *llr, size_t n, int nframes, double target,
                               float *scale, cudaStream_t s) {
-  k_int8_scale<<<nframes, 256, 0, s>>>(llr, n, target, scale);
-  return counted(cudaGetLastError(), 1);
+  return counted(launch_k(k_int8_scale, nframes, 256, 0, s, llr, n, target, scale), 1);
 }
 
 std::atomic<uint64_t> g_kernel_launches{0};
+std::atomic<int> g_pdl{0};
 
 size_t storage_bytes(int prec) { return prec == POLAR_FP32 ? 4 : (prec == POLAR_FP16 ? 2 : 1); }
 

@@ -695,6 +695,7 @@ __device__ __forceinline__ void subtree_body(const StParams &p, bool in_is_llr, 
 template <int NW, typename Tin, int FK, bool SC, bool UH>
 __global__ void __launch_bounds__(32 * NW) k_subtree(StParams p, bool in_is_llr) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  pdl_enter();
   subtree_body<NW, Tin, FK, SC, UH>(p, in_is_llr, blockIdx.x, smraw);
 }
 
@@ -714,8 +715,7 @@ cudaError_t launch_t(const SubtreeArgs &a, cudaStream_t s) {
   }
   StParams p{a.in,   a.in_stride, a.in_is_llr ? a.o : 0, a.cls, a.scale, a.mask, a.fv,
              a.xhat, a.uhat,      a.w_stride, a.o,     a.t,    a.r};
-  kern<<<a.nframes, 32 * NW, smem, s>>>(p, a.in_is_llr);
-  return counted(cudaGetLastError(), 1);
+  return counted(launch_k(kern, a.nframes, 32 * NW, smem, s, p, a.in_is_llr), 1);
 }
 
 template <typename S>

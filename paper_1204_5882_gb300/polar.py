@@ -75,6 +75,7 @@ def _load():
         "polar_build_frozen_set": ([U32, I, D, D, C.POINTER(P)], I),
         "polar_frozen_set_from_mask": ([U32, P, C.POINTER(P)], I),
         "polar_build_frozen_set_tv": ([U32, I, D, I, D, D, C.POINTER(P)], I),
+        "polar_build_frozen_set_sum": ([U32, I, D, D, C.POINTER(P)], I),
         "polar_frozen_set_query": ([P, C.POINTER(U32), C.POINTER(U64), P, C.POINTER(D)], I),
         "polar_frozen_set_free": ([P], None),
         "polar_llr_from_channel": ([I, D, P, I, P, SZ, P], I),
@@ -187,6 +188,15 @@ class FrozenSet:
         if getattr(self, "handle", None) is not None and _lib is not None:
             _lib.polar_frozen_set_free(self.handle)
             self.handle = None
+
+
+def polar_build_frozen_set_sum(log2n: int, channel: str, param: float,
+                               sum_pe_max: float = 0.1) -> FrozenSet:
+    """Bhattacharyya / GA set with K chosen by the sum rule (Sec. 3)."""
+    h = C.c_void_p()
+    _check("polar_build_frozen_set_sum", _lib.polar_build_frozen_set_sum(
+        int(log2n), CHANNEL[channel], float(param), float(sum_pe_max), C.byref(h)))
+    return FrozenSet(h.value)
 
 
 def polar_build_frozen_set_tv(log2n: int, channel: str, param: float, mu: int = 16,

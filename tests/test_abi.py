@@ -128,6 +128,18 @@ def test_library_degraded_construction_equals_oracle(P, case):
         P.polar_build_frozen_set_tv(n, ch, par, 3, rate, smax)
 
 
+@pytest.mark.parametrize("case", [(12, "biawgn", 1.0, 0.1), (16, "biawgn", 1 / 1.097, 0.1),
+                                  (14, "bsc", 0.02, 0.1), (10, "biawgn", 4.0, 0.01)])
+def test_library_sum_rule_construction_equals_oracle(P, case):
+    import oracle as O
+    from paper_1204_5882_gb300 import synth as S
+    n, ch, par, smax = case
+    fs = P.polar_build_frozen_set_sum(n, ch, par, smax)
+    fz, K, spe = O.frozen_set_sum(n, ch, par, smax)
+    assert fs.K == K and np.array_equal(S.unpack_bits(fs.mask(), 1 << n), fz)
+    assert fs.sum_pe == pytest.approx(spe, rel=1e-9)
+
+
 def test_frozen_set_from_mask_roundtrip(P):
     m = np.array([0xDEADBEEF, 0x0], dtype=np.uint32)
     fs = P.polar_frozen_set_from_mask(6, m)

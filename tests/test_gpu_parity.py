@@ -42,7 +42,7 @@ def words_np(t):
 @pytest.fixture(autouse=True)
 def default_config(P):
     saved = {k: P.polar_config_get(k)
-             for k in ("subtree_log2", "shortcuts", "graphs", "plain", "fuse")}
+             for k in ("subtree_log2", "shortcuts", "graphs", "plain", "fuse", "pdl")}
     yield
     for k, v in saved.items():
         P.polar_config_set(k, v)
@@ -150,9 +150,11 @@ def test_minsum_bitexact_small(P, n, kind, t):
     check_minsum(P, n, kind, F=2, seed=1000 * n + t + 7, llr_kind="bsc")
 
 
-@pytest.mark.parametrize("mode", ["no_shortcuts", "no_graphs", "plain", "no_fuse"])
+@pytest.mark.parametrize("mode", ["no_shortcuts", "no_graphs", "plain", "no_fuse", "no_pdl"])
 def test_minsum_bitexact_modes(P, mode):
-    if mode == "no_fuse":
+    if mode == "no_pdl":
+        P.polar_config_set("pdl", 0)
+    elif mode == "no_fuse":
         P.polar_config_set("fuse", 0)
     elif mode == "no_shortcuts":
         P.polar_config_set("shortcuts", 0)

@@ -123,6 +123,25 @@ def test_k_for_sum_rule_bruteforce():
                 assert bad[fz2 == 0].sum() > target
 
 
+def test_k_for_sum_log_rule_bruteforce():
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        lb = np.log(rng.exponential(0.01, 16))
+        lb[rng.integers(0, 16, 3)] = math.log(0.02)
+        for target in (0.0, 0.005, 0.03, 0.1, 10.0):
+            K = O.k_for_sum_log(lb, target)
+            fz = O.select_frozen(lb, K)
+            assert np.exp(lb[fz == 0]).sum() <= target * (1 + 1e-12)
+            if K < 16:
+                assert np.exp(lb[O.select_frozen(lb, K + 1) == 0]).sum() > target
+
+
+def test_frozen_set_sum_mode():
+    fz, K, s = O.frozen_set_sum(12, "biawgn", 1.0, 0.1)
+    assert int((fz == 0).sum()) == K and s <= 0.1
+    assert O.frozen_set_sum(12, "biawgn", 1.0, 1.0)[1] > K
+
+
 def test_frozen_set_tv_modes():
     fz, K, s = O.frozen_set_tv(12, "biawgn", 1.0, sum_pe_max=0.1)
     assert int((fz == 0).sum()) == K and s <= 0.1
