@@ -58,6 +58,8 @@ def parse():
                     help="served mixed stream: Poisson arrivals through the request server")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--inflight", type=int, default=48)
+    ap.add_argument("--persist-log2", type=int, default=None,
+                    help="subtree size of the persistent decoder / server (library default 13)")
     ap.add_argument("--serve-slots", action="store_true",
                     help="with --serve: also time the stream-slot server")
     ap.add_argument("--precision-sweep", action="store_true",
@@ -828,7 +830,10 @@ def run_figures(args):
             out["fig2_biawgn"].append(row)
             print(json.dumps({"fig2": row}), flush=True)
     print(json.dumps({"metric": "efficiency at sum P_e <= 0.1 (Figs. 1 and 2)",
-                      "construction": "degraded (Tal-Vardy)", "rows": out}), flush=True)
+                      "construction": {"fig1": f"degraded (Tal-Vardy), mu = {args.tv_mu}",
+                                       "fig2": "Gaussian approximation (degraded bound "
+                                               "beside it up to 2^23)"},
+                      "rows": out}), flush=True)
 
 
 # ------------------------------------------------------------------ precision sweep
@@ -935,6 +940,9 @@ def main():
     if args.subtree_log2 is not None and args.impl == "ours":
         from paper_1204_5882_gb300 import polar as P
         P.polar_config_set("subtree_log2", args.subtree_log2)
+    if args.persist_log2 is not None and args.impl == "ours":
+        from paper_1204_5882_gb300 import polar as P
+        P.polar_config_set("persist_log2", args.persist_log2)
     if args.fuse is not None and args.impl == "ours":
         from paper_1204_5882_gb300 import polar as P
         P.polar_config_set("fuse", args.fuse)

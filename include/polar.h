@@ -219,7 +219,10 @@ int polar_reveal(const polar_frozen_set *fs, int nframes, const uint32_t *x_dev,
  *                    also used as the partial-sum store while decoding;
  *   uhat_dev         packed output u_hat, or NULL;
  *   fkind            min-sum f (bit-exact against a float32 recursive SC)
- *                    or exact f = 2 atanh(tanh(a/2) tanh(b/2));
+ *                    or exact f = 2 atanh(tanh(a/2) tanh(b/2)), evaluated
+ *                    as sgn sgn [min + c(A+B) - c(|A-B|)] with c(d) =
+ *                    ln(1 + e^-d) from the SFU exponential and logarithm,
+ *                    identically at every level;
  *   prec             storage precision of the LLRs kept in device memory:
  *                    the channel LLRs as they are read and every level of
  *                    the recursion above the on-chip subtree size 2^t (FP16:

@@ -208,8 +208,13 @@ __device__ void decode_frame(const PFrame &fr, float *lv, unsigned char *smraw, 
   }
 }
 
+// Three CTAs per SM (168 registers): the frame loop around the inlined
+// subtree decoder would otherwise take ~240 registers and two CTAs per SM,
+// and the served throughput measured 3.5x lower.
+constexpr int kPersistMinBlocks = 3;
+
 template <int FK, bool UH>
-__global__ void __launch_bounds__(PT) k_persist(const PFrame *frames, uint32_t count,
+__global__ void __launch_bounds__(PT, kPersistMinBlocks) k_persist(const PFrame *frames, uint32_t count,
                                                 uint32_t *head, float *scratch,
                                                 uint64_t cta_floats, int S) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -271,7 +276,7 @@ __device__ uint32_t claim_frame(const ServeArgs &a) {
 }
 
 template <int FK>
-__global__ void __launch_bounds__(PT) k_serve(ServeArgs a) {
+__global__ void __launch_bounds__(PT, kPersistMinBlocks) k_serve(ServeArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ uint32_t s_idx;
   __shared__ __align__(16) PFrame s_fr;
@@ -301,16 +306,25 @@ __global__ void __launch_bounds__(PT) k_serve(ServeArgs a) {
   }
 }
 
+// The persistent CTAs leave only when the queue runs dry, so every CTA of
+// the grid must be resident at once: ask for the largest shared-memory
+// carveout (the occupancy query assumes it) and the dynamic size.
+template <typename K>
+cudaError_t prepare_persistent(K kern, size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       (int)cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess && smem > 48 * 1024)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return e;
+}
+
 template <int FK, bool UH>
 cudaError_t launch_pk(const PFrame *frames, uint32_t count, uint32_t *head, float *scratch,
                       uint64_t cta_floats, int t, int grid, cudaStream_t s) {
   const size_t smem = persistent_smem_bytes(t);
   auto kern = k_persist<FK, UH>;
-  if (smem > 48 * 1024) {
-    cudaError_t e =
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  cudaError_t e = prepare_persistent(kern, smem);
+  if (e != cudaSuccess) return e;
   kern<<<grid, PT, smem, s>>>(frames, count, head, scratch, cta_floats, upper_stages(smem));
   return counted(cudaGetLastError(), 1);
 }
@@ -319,10 +333,10 @@ template <int FK, bool UH>
 int occupancy(int t) {
   const size_t smem = persistent_smem_bytes(t);
   auto kern = k_persist<FK, UH>;
-  if (smem > 48 * 1024 &&
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-          cudaSuccess)
+  if (prepare_persistent(kern, smem) != cudaSuccess) {
+    cudaGetLastError();
     return 0;
+  }
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, PT, smem) != cudaSuccess) {
     cudaGetLastError();
@@ -335,10 +349,10 @@ template <int FK>
 int serve_occupancy(int t) {
   const size_t smem = persistent_smem_bytes(t);
   auto kern = k_serve<FK>;
-  if (smem > 48 * 1024 &&
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-          cudaSuccess)
+  if (prepare_persistent(kern, smem) != cudaSuccess) {
+    cudaGetLastError();
     return 0;
+  }
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, PT, smem) != cudaSuccess) {
     cudaGetLastError();
@@ -357,11 +371,8 @@ cudaError_t launch_serve(int fkind, ServeArgs a, int t, int grid, cudaStream_t s
   const size_t smem = persistent_smem_bytes(t);
   a.S = upper_stages(smem);
   auto kern = fkind == 0 ? k_serve<0> : k_serve<1>;
-  if (smem > 48 * 1024) {
-    cudaError_t e =
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  cudaError_t e = prepare_persistent(kern, smem);
+  if (e != cudaSuccess) return e;
   kern<<<grid, PT, smem, s>>>(a);
   return counted(cudaGetLastError(), 1);
 }
