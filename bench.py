@@ -75,6 +75,10 @@ def parse():
     ap.add_argument("--table1-oracle-frames", type=int, default=256)
     ap.add_argument("--table1-max-log2n", type=int, default=27)
     ap.add_argument("--tv-mu", type=int, default=16)
+    ap.add_argument("--mixed", action="store_true",
+                    help="heterogeneous batch: one persistent launch vs grouped launches")
+    ap.add_argument("--mixed-frames", type=int, default=20,
+                    help="frames per (length, channel) of the mixed batch")
     ap.add_argument("--figures", action="store_true",
                     help="efficiency curves of Figs. 1 and 2 from the degraded construction "
                          "(host only)")
@@ -676,6 +680,68 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ mixed batch
+def run_mixed(args):
+    """A heterogeneous batch (uneven N, both channels, frames shuffled):
+    one persistent launch (polar_sc_decode_batch with "persistent" = 1)
+    against the grouped launch sequences (one decode per run of equally
+    strided frames, "persistent" = 0).  Same bits either way."""
+    import torch
+
+    from paper_1204_5882_gb300 import polar as P
+
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    per = args.mixed_frames
+    frames, bits = [], 0
+    for j, n in enumerate((16, 18, 20, 22)):
+        for c, (ch, par, r) in enumerate((("bsc", 0.03, 0.75), ("biawgn", 1.0, 0.44))):
+            fs = P.polar_build_frozen_set(n, ch, par, r)
+            N = 1 << n
+            xs, ys = zip(*[S.device_frame(ch, par, N, 0x313ED + 2 * j + c, i, dev)
+                           for i in range(per)])
+            x, y = torch.stack(xs), torch.stack(ys)
+            fv = torch.empty_like(x)
+            P.polar_reveal(fs, per, x, fv)
+            llr = torch.empty(per, N, dtype=torch.float32, device=dev)
+            P.polar_llr_from_channel(ch, par, y, llr)
+            xh = torch.empty_like(x)
+            frames += [(fs, llr[i], fv[i], xh[i], None) for i in range(per)]
+            bits += per * N
+    order = np.random.default_rng(0).permutation(len(frames))
+    frames = [frames[i] for i in order]
+    torch.cuda.synchronize()
+    res = {}
+    for mode, label in ((1, "persistent"), (0, "grouped")):
+        P.polar_config_set("persistent", mode)
+        P.polar_sc_decode_batch(frames, "minsum", "fp32", stream)       # warm-up
+        stream.synchronize()
+        reps = args.steps if mode else max(1, min(args.steps, 3))      # grouped: ~1 s each
+        l0 = P.polar_kernel_launches()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            P.polar_sc_decode_batch(frames, "minsum", "fp32", stream)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b) / reps
+        res[label] = {"mbit_s": bits / (ms / 1e3) / 1e6, "ms_per_batch": ms,
+                      "kernel_launches_per_batch": (P.polar_kernel_launches() - l0) / reps,
+                      "x_hat": [f[3].clone() for f in frames]}
+    same = all(torch.equal(p_, g_) for p_, g_ in zip(res["persistent"].pop("x_hat"),
+                                                     res["grouped"].pop("x_hat")))
+    P.polar_config_set("persistent", 1)
+    print(json.dumps({"metric": "decoded Mbit/s of a heterogeneous batch", "unit": UNIT,
+                      "value": res["persistent"]["mbit_s"], "data": "synthetic",
+                      "config": {"workload": "mixed_batch", "frames": len(frames),
+                                 "N": "2^16, 2^18, 2^20, 2^22 (equal counts)",
+                                 "channels": "BSC p 0.03 R 0.75 / BI-AWGN sigma^2 1 R 0.44",
+                                 "order": "shuffled", "persist_log2":
+                                     P.polar_config_get("persist_log2")},
+                      "results": res, "same_bits": same}), flush=True)
+
+
 # ------------------------------------------------------------------ Table 1
 # The paper's Table 1 rows (one i5-670 core, fixed point, density-evolution
 # frozen sets with the frame error rate bounded at 0.1): channel, parameter
@@ -741,6 +807,7 @@ def run_table1(args):
             frames = max(8, args.table1_frames // 64)
         B = min(frames, 256 if n <= 16 else (64 if n <= 20 else (16 if n <= 24 else 8)))
         err = {"minsum": 0, "exact": 0}
+        rejected = {"minsum": 0, "exact": 0}
         ms = {"minsum": 0.0, "exact": 0.0}
         done, tuned = 0, None
         sample = []
@@ -757,6 +824,9 @@ def run_table1(args):
             xh = torch.empty_like(x)
             if tuned is None and b == B:
                 tuned = P.polar_autotune(fs, b, llr, fv, xh, "minsum", "fp32", stream)
+            hx = torch.empty(b, dtype=torch.int64, device=dev)
+            hb = torch.empty(b, dtype=torch.int64, device=dev)
+            P.polar_frame_hash(n, b, x, 0x5EED_CAFE + ri, hx, stream)     # Alice's hashes
             for fk in ("minsum", "exact"):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 torch.cuda.synchronize()
@@ -766,6 +836,9 @@ def run_table1(args):
                 e1.synchronize()
                 ms[fk] += e0.elapsed_time(e1)
                 err[fk] += int((xh != x).any(dim=1).sum().item())
+                P.polar_frame_hash(n, b, xh, 0x5EED_CAFE + ri, hb, stream)  # Bob's, verified
+                stream.synchronize()
+                rejected[fk] += int((hb != hx).sum().item())
             if n <= 16 and len(sample) < args.table1_oracle_frames:
                 take = min(b, args.table1_oracle_frames - len(sample))
                 yb = y[:take].cpu().numpy()
@@ -783,6 +856,13 @@ def run_table1(args):
                "mbit_s_minsum": frames * N / (ms["minsum"] / 1e3) / 1e6,
                "mbit_s_exact": frames * N / (ms["exact"] / 1e3) / 1e6,
                "schedule": {"subtree_log2": tuned[0], "fused": bool(tuned[1])} if tuned else None,
+               "verification": {"frames_rejected_by_hash": rejected,
+                                "what": "64-bit keyed hashes of x and x_hat compared"},
+               "key_rate_per_raw_bit_exact": {
+                   "value": P.polar_key_rate(1.0, err["exact"] / frames, fs.K / N / C, C, 0.0),
+                   "what": "alpha (1 - FER) (beta I - S) with alpha = 1 (the decoder outruns "
+                           "any QKD input rate), I = C, S = 0 (Eve's information is "
+                           "protocol-specific)"},
                "paper": {"beta": p_beta, "fer": p_fer, "mb_s_one_core": p_mbs}}
         if sample:
             fz = S.unpack_bits(fs.mask(), N)
@@ -956,6 +1036,8 @@ def main():
         run_table1(args)
     elif args.figures:
         run_figures(args)
+    elif args.mixed:
+        run_mixed(args)
     else:
         run_ours(args)
 

@@ -304,6 +304,27 @@ int polar_tune_save(const char *path);
 int polar_tune_load(const char *path);
 void polar_tune_clear(void);
 
+/* ------------------------------------------------------- verification, rate */
+
+/* Keyed hash of each of nframes packed frames of 2^log2n bits (words_dev:
+ * [nframes][max(1, N/32)] words; hash_dev: nframes uint64, device).  For
+ * the verification step of Sec. 2.1: Alice and Bob hash x and x_hat with a
+ * shared key and discard the blocks whose hashes differ.  h = sum_i w_i c_i
+ * mod (2^61 - 1) over the frame's 32-bit words w_i, with c_i the SplitMix64
+ * output number i of the key, reduced mod 2^61 - 1; with uniform
+ * coefficients two different frames collide with probability 2^-61.
+ * Bits of a frame shorter than a word beyond N must be zero.  EINVAL: bad
+ * sizes, NULL or misaligned pointers. */
+int polar_frame_hash(uint32_t log2n, int nframes, const uint32_t *words_dev, uint64_t key,
+                     uint64_t *hash_dev, void *stream);
+
+/* Secret key rate with imperfect error correction (Sec. 2.1):
+ * K = alpha (1 - FER) (beta I(x:y) - S(x:E)), alpha = the decoder's output
+ * rate over the data rate fed to it (at most 1), beta = R / C.  Host
+ * arithmetic only. */
+double polar_key_rate(double alpha, double fer, double beta, double mutual_info,
+                      double eve_info);
+
 /* ---------------------------------------------------------------- serving */
 
 /* Continuous-batching request server (the serving pattern around the SC
@@ -362,7 +383,7 @@ int polar_server_create(const polar_server_config *cfg, polar_server **out);
 /* Queue a request; *ticket identifies it.  EINVAL: bad request (checked on
  * the host; persistent mode also refuses codes longer than max_log2n and
  * requests of more frames than half the ring, which holds
- * max(1024, 4 * resident CTAs) frames rounded up to a power of two);
+ * max(8192, 16 * resident CTAs) frames rounded up to a power of two);
  * EBUSY: the queue holds max_queue requests (admission refused, retry
  * later).  The caller keeps every buffer alive until completion, and
  * its inputs must already be complete on the device when submit is called:

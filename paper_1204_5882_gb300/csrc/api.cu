@@ -796,6 +796,21 @@ int polar_llr_from_channel(polar_channel ch, double param, const void *y_dev, in
   return POLAR_EINVAL;
 }
 
+int polar_frame_hash(uint32_t log2n, int nframes, const uint32_t *words_dev, uint64_t key,
+                     uint64_t *hash_dev, void *stream) {
+  if (log2n < 1 || log2n > 27 || nframes < 1 || !words_dev || !hash_dev) return POLAR_EINVAL;
+  if (!aligned(words_dev, 4) || !aligned(hash_dev, 8)) return POLAR_EINVAL;
+  const size_t W = log2n >= 5 ? (size_t(1) << (log2n - 5)) : 1;
+  CK(launch_frame_hash(words_dev, W, W, nframes, key, hash_dev,
+                       static_cast<cudaStream_t>(stream)));
+  return POLAR_OK;
+}
+
+double polar_key_rate(double alpha, double fer, double beta, double mutual_info,
+                      double eve_info) {
+  return alpha * (1.0 - fer) * (beta * mutual_info - eve_info);
+}
+
 int polar_encode(uint32_t log2n, int nframes, const uint32_t *in_dev, uint32_t *out_dev,
                  void *stream) {
   if (log2n < 1 || log2n > 27 || nframes < 1 || !in_dev || !out_dev) return POLAR_EINVAL;

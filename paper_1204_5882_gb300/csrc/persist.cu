@@ -208,9 +208,9 @@ __device__ void decode_frame(const PFrame &fr, float *lv, unsigned char *smraw, 
   }
 }
 
-// Three CTAs per SM (168 registers): the frame loop around the inlined
-// subtree decoder would otherwise take ~240 registers and two CTAs per SM,
-// and the served throughput measured 3.5x lower.
+// Three CTAs per SM (168 registers, a few spills): the frame loop around the
+// inlined subtree decoder would otherwise take ~240 registers and leave room
+// for two CTAs per SM.
 constexpr int kPersistMinBlocks = 3;
 
 template <int FK, bool UH>

@@ -163,6 +163,10 @@ cudaError_t launch_subtree(const SubtreeArgs &a, cudaStream_t s);
 
 size_t storage_bytes(int prec);
 
+// Keyed hash of each frame's packed words (verification of decoded blocks).
+cudaError_t launch_frame_hash(const uint32_t *words, size_t stride_w, size_t nwords,
+                              int nframes, uint64_t key, uint64_t *out, cudaStream_t s);
+
 // --- persistent decoder (persist.cu) ------------------------------------------
 // One frame of a persistent launch.  Levels t..n-1 of the frame being decoded
 // live in the scratch of the CTA that claimed it.

@@ -77,8 +77,8 @@ struct Ring {
   bool stopping = false;                  // stop word set for the running launch
   Clock::time_point last_busy;            // last time frames were outstanding
   uint32_t published = 0;                 // frames published (tail)
-  std::deque<uint32_t> out;               // published frame indices, oldest first
-  std::vector<uint8_t> seen;              // per entry: completion observed
+  std::vector<uint32_t> out;              // published frames not yet complete, any order
+  std::vector<uint8_t> seen;              // per entry: free (its last frame completed)
   std::vector<uint64_t> ticket;           // per entry: request ticket
   std::unordered_map<uint64_t, int> left; // ticket -> frames not yet complete
 };
@@ -207,20 +207,24 @@ void finish_ticket(polar_server *s, uint64_t ticket, int status) {
 }
 
 // Completions: every published frame whose completion word has arrived.
+// Frames finish in any order; each frees its own ring entry.
 void ring_collect(polar_server *s) {
   Ring &r = s->pr;
-  for (uint32_t idx : r.out) {
-    const uint32_t e = idx & (r.R - 1);
-    if (r.seen[e]) continue;
-    if (__atomic_load_n(r.done + e, __ATOMIC_ACQUIRE) != idx + 1) continue;
+  for (size_t k = 0; k < r.out.size();) {
+    const uint32_t idx = r.out[k], e = idx & (r.R - 1);
+    if (__atomic_load_n(r.done + e, __ATOMIC_ACQUIRE) != idx + 1) {
+      ++k;
+      continue;
+    }
     r.seen[e] = 1;
     auto it = r.left.find(r.ticket[e]);
     if (it != r.left.end() && --it->second == 0) {
       finish_ticket(s, it->first, POLAR_OK);
       r.left.erase(it);
     }
+    r.out[k] = r.out.back();
+    r.out.pop_back();
   }
-  while (!r.out.empty() && r.seen[r.out.front() & (r.R - 1)]) r.out.pop_front();
 }
 
 // Publishes the oldest pending requests while the ring has room.
@@ -232,8 +236,9 @@ void ring_publish(polar_server *s) {
   while (!s->queue.empty()) {
     Pending &p = s->queue.front();
     const uint32_t nf = (uint32_t)p.req.nframes;
-    const uint32_t oldest = r.out.empty() ? r.published : r.out.front();
-    if (r.published + nf - oldest > r.R) break;           // ring full
+    bool room = true;                                      // the next nf entries are free
+    for (uint32_t f = 0; f < nf && room; ++f) room = r.seen[(r.published + f) & (r.R - 1)];
+    if (!room) break;
     polar_frozen_set *fs = const_cast<polar_frozen_set *>(p.req.fs);
     const int n = (int)fs->log2n, t = std::min(n, r.t);
     cudaError_t e = cudaSuccess;
@@ -396,8 +401,10 @@ int ring_create(polar_server *s) {
   uint64_t fit = r.cta_floats ? c.mem_budget / (r.cta_floats * sizeof(float)) : ~uint64_t(0);
   r.grid = (int)std::min<uint64_t>({(uint64_t)per_sm * sms, (uint64_t)c.max_inflight, fit});
   if (r.grid < 1) return POLAR_ENOMEM;
-  r.R = 1024;
-  while (r.R < 4u * (uint32_t)r.grid) r.R *= 2;
+  // frames are published in order but finish in any order: a generous ring
+  // keeps a long frame's entry from holding back the next publications
+  r.R = 8192;
+  while (r.R < 16u * (uint32_t)r.grid) r.R *= 2;
   r.seen.assign(r.R, 1);
   r.ticket.assign(r.R, 0);
   auto fail = [&](cudaError_t e) {

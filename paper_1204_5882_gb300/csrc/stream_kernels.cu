@@ -542,6 +542,56 @@ cudaError_t launch_int8_scale(const float *llr, size_t n, int nframes, double ta
   return counted(launch_k(k_int8_scale, nframes, 256, 0, s, llr, n, target, scale), 1);
 }
 
+// ---------------------------------------------------------------- verification
+// Keyed linear hash of a frame's packed bits, for the verification step that
+// discards wrongly decoded blocks (Sec. 2.1): h = sum_i w_i c_i mod p,
+// p = 2^61 - 1, w_i the frame's 32-bit words, c_i the SplitMix64 output for
+// (key, i) reduced mod p.  Two different frames collide with probability
+// 1/p when the coefficients are uniform.  One CTA per frame.
+constexpr uint64_t kHashP = (uint64_t(1) << 61) - 1;
+
+__device__ __forceinline__ uint64_t hash_coef(uint64_t key, uint64_t i) {
+  uint64_t z = key + (i + 1) * 0x9E3779B97F4A7C15ull;      // SplitMix64 step i
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  z = (z & kHashP) + (z >> 61);
+  return z >= kHashP ? z - kHashP : z;
+}
+
+__device__ __forceinline__ uint64_t hash_mulmod(uint64_t w, uint64_t c) {   // w < 2^32, c < p
+  const uint64_t lo = w * c, hi = __umul64hi(w, c);
+  uint64_t r = (lo & kHashP) + ((hi << 3) | (lo >> 61));
+  return r >= kHashP ? r - kHashP : r;
+}
+
+__device__ __forceinline__ uint64_t hash_addmod(uint64_t a, uint64_t b) {
+  const uint64_t r = a + b;
+  return r >= kHashP ? r - kHashP : r;
+}
+
+__global__ void k_frame_hash(const uint32_t *__restrict__ words, size_t stride, size_t nw,
+                             uint64_t key, uint64_t *__restrict__ out) {
+  __shared__ uint64_t part[256];
+  const uint32_t *w = words + blockIdx.x * stride;
+  uint64_t acc = 0;
+  for (size_t i = threadIdx.x; i < nw; i += blockDim.x)
+    acc = hash_addmod(acc, hash_mulmod(w[i], hash_coef(key, i)));
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  for (unsigned h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) part[threadIdx.x] = hash_addmod(part[threadIdx.x], part[threadIdx.x + h]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = part[0];
+}
+
+cudaError_t launch_frame_hash(const uint32_t *words, size_t stride_w, size_t nwords,
+                              int nframes, uint64_t key, uint64_t *out, cudaStream_t s) {
+  k_frame_hash<<<nframes, 256, 0, s>>>(words, stride_w, nwords, key, out);
+  return counted(cudaGetLastError(), 1);
+}
+
 std::atomic<uint64_t> g_kernel_launches{0};
 std::atomic<int> g_pdl{0};
 

@@ -91,6 +91,8 @@ def _load():
         "polar_tune_save": ([C.c_char_p], I),
         "polar_tune_load": ([C.c_char_p], I),
         "polar_tune_clear": ([], None),
+        "polar_frame_hash": ([U32, I, P, U64, P, P], I),
+        "polar_key_rate": ([D, D, D, D, D], D),
         "polar_server_create": ([C.POINTER(ServerConfig), C.POINTER(P)], I),
         "polar_server_submit": ([P, C.POINTER(Request), C.POINTER(U64)], I),
         "polar_server_poll": ([P, U64, C.POINTER(Result)], I),
@@ -284,6 +286,20 @@ def polar_sc_decode_many_noalloc(fs: FrozenSet, nframes: int, llr, fval, xhat, u
     _check("polar_sc_decode_many_noalloc", _lib.polar_sc_decode_many_noalloc(
         fs.handle, int(nframes), _ptr(llr), _ptr(fval), _ptr(xhat), _ptr(uhat), FKIND[fkind],
         PREC[prec], _stream(stream)))
+
+
+# ------------------------------------------------------------------ verification
+def polar_frame_hash(log2n: int, nframes: int, words, key: int, out, stream=None):
+    """Keyed hash of each packed frame into out (uint64 / int64 tensor)."""
+    _check("polar_frame_hash", _lib.polar_frame_hash(
+        int(log2n), int(nframes), _ptr(words), int(key) & (2 ** 64 - 1), _ptr(out),
+        _stream(stream)))
+
+
+def polar_key_rate(alpha: float, fer: float, beta: float, mutual_info: float,
+                   eve_info: float) -> float:
+    return _lib.polar_key_rate(float(alpha), float(fer), float(beta), float(mutual_info),
+                               float(eve_info))
 
 
 # ------------------------------------------------------------------ autotuning

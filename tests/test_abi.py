@@ -81,6 +81,11 @@ def test_argument_errors_are_host_side(P):
     assert L.polar_llr_from_channel(1, 1.0, 16, 0, 16, 0, None) == P.POLAR_OK   # empty
     assert L.polar_encode(0, 1, 16, 16, None) == P.POLAR_EINVAL
     assert L.polar_encode(28, 1, 16, 16, None) == P.POLAR_EINVAL
+    # verification hash: sizes, null and misaligned pointers; key-rate formula
+    assert L.polar_frame_hash(0, 1, 16, 1, 16, None) == P.POLAR_EINVAL
+    assert L.polar_frame_hash(10, 1, None, 1, 16, None) == P.POLAR_EINVAL
+    assert L.polar_frame_hash(10, 1, 16, 1, 12, None) == P.POLAR_EINVAL
+    assert P.polar_key_rate(0.5, 0.1, 0.9, 0.8, 0.3) == pytest.approx(0.5 * 0.9 * (0.9 * 0.8 - 0.3))
     # persistent decoder: empty queue, null table, non-float32 storage
     desc = (P.FrameDesc * 1)(P.FrameDesc(fs.handle.value, 16, 16, 16, None))
     assert L.polar_sc_decode_persistent(0, desc, 0, 0, None) == P.POLAR_EINVAL

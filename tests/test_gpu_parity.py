@@ -346,3 +346,37 @@ def test_table1_largest_code_2_27_sampled(P):
     fvb = S.unpack_bits(words_np(fv[0]), N)
     _, ox = O.sc_decode(L0, ofz, fvb, "minsum")
     assert np.array_equal(S.unpack_bits(words_np(xh[0]), N), ox)
+
+
+# ------------------------------------------------------------------ verification hash
+def _hash_reference(words, key):
+    """The frame hash by its definition, with Python integers."""
+    M64, P61 = 2 ** 64 - 1, 2 ** 61 - 1
+    h = 0
+    for i, w in enumerate(words):
+        z = (key + (i + 1) * 0x9E3779B97F4A7C15) & M64
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M64
+        z ^= z >> 31
+        z = (z & P61) + (z >> 61)
+        if z >= P61:
+            z -= P61
+        h = (h + int(w) * z) % P61
+    return h
+
+
+@pytest.mark.parametrize("n", [3, 5, 12, 16])
+def test_frame_hash_matches_definition_and_detects_errors(P, n):
+    N, F, key = 1 << n, 4, 0x1234_5678_9ABC_DEF0
+    rng = np.random.default_rng(n)
+    bits = rng.integers(0, 2, (F, N)).astype(np.uint8)
+    bits[1] = bits[0]                                   # identical frames
+    bits[2] = bits[0]
+    bits[2][N // 3] ^= 1                                # one flipped bit
+    words = np.stack([S.pack_bits(r) for r in bits])
+    out = torch.zeros(F, dtype=torch.int64, device=DEV)
+    P.polar_frame_hash(n, F, to_dev_words(words), key, out)
+    torch.cuda.synchronize()
+    got = [int(v) & (2 ** 64 - 1) for v in out.cpu().numpy()]
+    assert got == [_hash_reference(w, key) for w in words]
+    assert got[0] == got[1] and got[0] != got[2]
