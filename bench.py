@@ -826,6 +826,7 @@ def run_table1(args):
                 tuned = P.polar_autotune(fs, b, llr, fv, xh, "minsum", "fp32", stream)
             hx = torch.empty(b, dtype=torch.int64, device=dev)
             hb = torch.empty(b, dtype=torch.int64, device=dev)
+            torch.cuda.synchronize()          # x, fv and llr come from torch's stream
             P.polar_frame_hash(n, b, x, 0x5EED_CAFE + ri, hx, stream)     # Alice's hashes
             for fk in ("minsum", "exact"):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
