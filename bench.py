@@ -89,6 +89,8 @@ def parse():
                     help="override the subtree size t (library default 14)")
     ap.add_argument("--fuse", type=int, choices=[0, 1], default=None,
                     help="override fused (1) or per-level (0) streamed steps")
+    ap.add_argument("--prologue", type=int, choices=[0, 1], default=None,
+                    help="override: the subtree kernel takes its parent's streamed step (1)")
     return ap.parse_args()
 
 
@@ -305,10 +307,36 @@ def measure_n24(args, P, dev, steps=5, warmup=2):
         stream.synchronize()
         ms = sum(a.elapsed_time(b) for a, b in ev) / steps
         fer = float((xh != xd).any(dim=1).float().mean().item())
+        # per-kernel pass (eager launches with events), as for the main workload
+        P.polar_config_set("profile", 2)
+        P.polar_profile_reset()
+        flush.zero_()
+        step()
+        stream.synchronize()
+        prof = {k: P.polar_profile_read(k) for k in P.PROFILE_KINDS}
+        P.polar_config_set("profile", 0)
+        kinds = ["stream_f", "stream_g", "chain"]
+        sms = sum(prof[k][0] for k in kinds)
+        sby = sum(prof[k][2] for k in kinds)
+        sn = sum(prof[k][1] for k in kinds)
+        peaks = measured_peaks()
+        hbm = peaks["hbm_gbs"] if peaks else 6800.0
+        streamed = None
+        if sms > 0 and sn:
+            ach = sby / (sms / 1e3) / 1e9
+            streamed = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                        "frac": ach / hbm, "launches": sn, "avg_launch_us": sms / sn * 1e3,
+                        "alg_bytes_per_launch": sby / sn, "kernels": kinds,
+                        "timing": "eager launches with events",
+                        "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks
+                        else "fallback 6.8 TB/s"}
         out = {"workload": w.name, "value": F * N / (ms / 1e3) / 1e6, "unit": UNIT,
                "ms_per_step": ms, "steps": steps, "frames": F, "fer": fer,
-               "schedule": {"subtree_log2": tuned[0], "fused": bool(tuned[1])} if tuned
+               "schedule": {"subtree_log2": tuned[0], "fused": bool(tuned[1] & 1),
+                            "subtree_takes_parent_step": bool(tuned[1] & 2)} if tuned
                else "default",
+               "roofline_streamed": streamed,
+               "kernel_time_ms": {k: {"ms": prof[k][0], "launches": prof[k][1]} for k in prof},
                "inputs": "drawn on the device (torch Philox, seeded per frame)"}
         if args.plain_n24:
             P.polar_config_set("plain", 1)
@@ -542,8 +570,10 @@ def run_ours(args):
             "data": "synthetic",
             "config": config_of(w, args, {"subtree_log2": tuned[0] if tuned else
                                           (args.subtree_log2 or 14),
-                                          "fused_streamed_steps": bool(tuned[1]) if tuned else
+                                          "fused_streamed_steps": bool(tuned[1] & 1) if tuned else
                                           (args.fuse != 0),
+                                          "subtree_takes_parent_step": bool(tuned[1] & 2)
+                                          if tuned else bool(args.prologue),
                                           "schedule": "polar_autotune" if tuned else "default"}),
             "roofline": roof, "roofline_streamed": hbm_roof(["stream_f", "stream_g", "chain"]),
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
@@ -856,7 +886,8 @@ def run_table1(args):
                "fer_exact": _wilson(err["exact"], frames),
                "mbit_s_minsum": frames * N / (ms["minsum"] / 1e3) / 1e6,
                "mbit_s_exact": frames * N / (ms["exact"] / 1e3) / 1e6,
-               "schedule": {"subtree_log2": tuned[0], "fused": bool(tuned[1])} if tuned else None,
+               "schedule": {"subtree_log2": tuned[0], "fused": bool(tuned[1] & 1),
+                            "subtree_takes_parent_step": bool(tuned[1] & 2)} if tuned else None,
                "verification": {"frames_rejected_by_hash": rejected,
                                 "what": "64-bit keyed hashes of x and x_hat compared"},
                "key_rate_per_raw_bit_exact": {
@@ -1027,6 +1058,9 @@ def main():
     if args.fuse is not None and args.impl == "ours":
         from paper_1204_5882_gb300 import polar as P
         P.polar_config_set("fuse", args.fuse)
+    if args.prologue is not None and args.impl == "ours":
+        from paper_1204_5882_gb300 import polar as P
+        P.polar_config_set("prologue", args.prologue)
     if args.impl == "reference":
         run_reference(args)
     elif args.serve:

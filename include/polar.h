@@ -89,6 +89,10 @@ const char *polar_last_error_string(void);
  *   "fuse"          1 = each streamed f/g step and the f steps continuing it
  *                   run as one fused column kernel (default); 0 = one launch
  *                   per step.
+ *   "prologue"      1 = with float32 storage, each subtree kernel performs
+ *                   the streamed step that produces its input (the f or g
+ *                   from level t + 1) while loading, instead of a separate
+ *                   launch; 0 (default).  Results do not depend on it.
  *   "int8_target"   INT8 storage: the per-frame scale is the power of two
  *                   2^rint(log2(target / mean|L|)) (mean in double over the
  *                   frame's channel LLRs); 1..64, default 8.
@@ -286,13 +290,15 @@ int polar_sc_decode_persistent(int nframes, const polar_frame_desc *frames,
 
 /* Times the decode of this batch (contiguous as for polar_sc_decode_many)
  * under each candidate schedule -- subtree sizes t = 12, 13, 14 (float32
- * storage only: with FP16 / INT8 the rounded levels depend on t) with fused
- * and unfused streamed steps -- and keeps the fastest for the batch shape
+ * storage only: with FP16 / INT8 the rounded levels depend on t), fused and
+ * unfused streamed steps, and (float32) with or without the subtree kernel
+ * taking its parent's step -- and keeps the fastest for the batch shape
  * (device, log2 N, nframes, fkind, prec).  While the "autotune" option is 1
  * (default), later decodes of that shape use it.  Synchronous on `stream`;
- * the batch's outputs are overwritten with valid decodes.  Any of best_t,
- * best_fuse, best_ms may be NULL.  Decisions do not depend on the schedule
- * (float32). */
+ * the batch's outputs are overwritten with valid decodes.  *best_fuse
+ * receives the schedule flags (bit 0: fused streamed steps, bit 1: the
+ * subtree takes its parent's step).  Any of best_t, best_fuse, best_ms may
+ * be NULL.  Decisions do not depend on the schedule (float32). */
 int polar_autotune(const polar_frozen_set *fs, int nframes, const float *llr_dev,
                    const uint32_t *frozen_vals_dev, uint32_t *xhat_dev,
                    polar_fkind fkind, polar_prec prec, void *stream, int *best_t,

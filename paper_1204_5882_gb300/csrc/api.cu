@@ -25,12 +25,14 @@ struct Config {
   std::atomic<long> profile{0};
   std::atomic<long> int8_target{8};
   std::atomic<long> fuse{1};
+  std::atomic<long> prologue{0};
   std::atomic<long> autotune{1};
   std::atomic<long> persistent{1};
 };
 
 // ---------------------------------------------------------------- autotuning
-// Best (subtree size, fused streamed steps) per batch shape, found by
+// Best (subtree size, schedule flags: 1 = fused streamed steps, 2 = the
+// subtree kernel takes its parent's step) per batch shape, found by
 // polar_autotune; used by later decodes of that shape while "autotune" is 1.
 struct TuneKey {
   int dev, log2n, nframes, fkind, prec;
@@ -214,6 +216,30 @@ inline size_t workspace_bytes(int n, int t, int nframes, int prec) {
   return scale_region(nframes, prec) + lv;
 }
 
+// One streamed f or g step (level op.k -> op.k - 1) over every frame.
+int run_step(const Exec &x, const Op &op, cudaStream_t s, bool prof) {
+  const Group &g = *x.g;
+  const int n = x.n, k = op.k;
+  const uint64_t N = uint64_t(1) << n;
+  const size_t W = N >= 32 ? N / 32 : 1;
+  const double F = g.nframes, sb = (double)storage_bytes(g.prec);
+  float *scale = scale_ptr(x);
+  const bool top = (k == n);
+  const void *in = top ? static_cast<const void *>(g.llr) : level_ptr(x, k);
+  const size_t ins = top ? N : (size_t(1) << k);
+  void *out = level_ptr(x, k - 1);
+  const uint64_t h = uint64_t(1) << (k - 1);
+  const double inb = top ? 4.0 : sb;
+  ProfScope ps(prof, op.kind == OP_F ? 1 : 2,
+               F * (2.0 * h * inb + h * sb + (op.kind == OP_G ? h / 8.0 : 0.0)), s);
+  if (op.kind == OP_F) {
+    CK(launch_stream_f(g.prec, g.fkind, in, ins, top, out, h, h, g.nframes, scale, s));
+  } else {
+    CK(launch_stream_g(g.prec, in, ins, top, out, h, h, g.xhat, W, op.o, g.nframes, scale, s));
+  }
+  return POLAR_OK;
+}
+
 int run_ops(const Exec &x, cudaStream_t s, bool prof) {
   const Group &g = *x.g;
   const int n = x.n, t = x.t;
@@ -222,32 +248,30 @@ int run_ops(const Exec &x, cudaStream_t s, bool prof) {
   const double F = g.nframes, sb = (double)storage_bytes(g.prec);
   float *scale = scale_ptr(x);
   if (scale) CK(launch_int8_scale(g.llr, N, g.nframes, (double)g_cfg.int8_target.load(), scale, s));
-  for (const Op &op : x.plan->ops) {
+  for (const Op &op0 : x.plan->ops) {
+    Op op = op0;
+    if (op.kind == OP_ST && op.pad && g.prec != POLAR_FP32) {
+      // reduced storage: the parent's step stays a streamed launch
+      const Op step{(uint8_t)(op.pad == 1 ? OP_F : OP_G), (uint8_t)(t + 1), 0, 0,
+                    op.pad == 1 ? op.o : op.o - (uint64_t(1) << t)};
+      const int rc = run_step(x, step, s, prof);
+      if (rc) return rc;
+      op.pad = 0;
+    }
     switch (op.kind) {
       case OP_F:
       case OP_G: {
-        const int k = op.k;
-        const bool top = (k == n);
-        const void *in = top ? static_cast<const void *>(g.llr) : level_ptr(x, k);
-        const size_t ins = top ? N : (size_t(1) << k);
-        void *out = level_ptr(x, k - 1);
-        const uint64_t h = uint64_t(1) << (k - 1);
-        const double inb = top ? 4.0 : sb;
-        ProfScope ps(prof, op.kind == OP_F ? 1 : 2,
-                     F * (2.0 * h * inb + h * sb + (op.kind == OP_G ? h / 8.0 : 0.0)), s);
-        if (op.kind == OP_F) {
-          CK(launch_stream_f(g.prec, g.fkind, in, ins, top, out, h, h, g.nframes, scale, s));
-        } else {
-          CK(launch_stream_g(g.prec, in, ins, top, out, h, h, g.xhat, W, op.o, g.nframes, scale,
-                             s));
-        }
+        const int rc = run_step(x, op, s, prof);
+        if (rc) return rc;
         break;
       }
       case OP_ST: {
         SubtreeArgs a;
-        a.in_is_llr = (n == t);
-        a.in = a.in_is_llr ? static_cast<const void *>(g.llr) : level_ptr(x, t);
-        a.in_stride = a.in_is_llr ? N : (size_t(1) << t);
+        a.pre = op.pad;
+        const int kin = op.pad ? t + 1 : t;   // level the kernel reads
+        a.in_is_llr = (n == kin);
+        a.in = a.in_is_llr ? static_cast<const void *>(g.llr) : level_ptr(x, kin);
+        a.in_stride = a.in_is_llr ? N : (size_t(1) << kin);
         a.mask = x.dmask;
         a.cls = x.dclass ? x.dclass + (op.o >> t) * 2 * class_words(t) : nullptr;
         a.scale = scale;
@@ -266,7 +290,9 @@ int run_ops(const Exec &x, cudaStream_t s, bool prof) {
         double cb = 0;
         for (int m = 0; m < op.r; ++m) cb += 3.0 * double(uint64_t(1) << (t + m)) / 8.0;
         ProfScope ps(prof, 3,
-                     F * (T * (a.in_is_llr ? 4.0 : sb) + T / 8.0 * (g.uhat ? 4 : 3) + cb), s);
+                     F * ((op.pad ? 2.0 : 1.0) * T * (a.in_is_llr ? 4.0 : sb) +
+                          T / 8.0 * (g.uhat ? 4 : 3) + (op.pad == 2 ? T / 8.0 : 0.0) + cb),
+                     s);
         CK(launch_subtree(a, s));
         break;
       }
@@ -309,7 +335,7 @@ int current_device(int *dev) {
 }
 
 struct Opts {
-  bool plain, shortcuts, graphs, profile, fuse;
+  bool plain, shortcuts, graphs, profile, fuse, prologue;
   int subtree_log2;
 };
 
@@ -320,6 +346,7 @@ Opts current_opts() {
   o.graphs = !o.plain && g_cfg.graphs.load() != 0;
   o.profile = g_cfg.profile.load() != 0;
   o.fuse = !o.plain && g_cfg.fuse.load() != 0;
+  o.prologue = !o.plain && g_cfg.prologue.load() != 0;
   o.subtree_log2 = (int)g_cfg.subtree_log2.load();
   return o;
 }
@@ -334,7 +361,8 @@ Opts opts_for(const polar_frozen_set *fs, int nframes, int fkind, int prec) {
   auto it = g_tune.find(TuneKey{dev, (int)fs->log2n, nframes, fkind, prec});
   if (it != g_tune.end()) {
     o.subtree_log2 = it->second.t;
-    o.fuse = it->second.fuse != 0;
+    o.fuse = (it->second.fuse & 1) != 0;
+    o.prologue = (it->second.fuse & 2) != 0;
   }
   return o;
 }
@@ -353,7 +381,7 @@ int decode_group(const Group &g, cudaStream_t s, const Opts &opt) {
   cudaError_t e;
   const uint32_t *dmask = device_mask(fs, dev, &e);
   if (!dmask) return e == cudaErrorMemoryAllocation ? POLAR_ENOMEM : cuda_fail(e);
-  std::shared_ptr<Plan> plan = get_plan(fs, t, shortcuts, opt.fuse);
+  std::shared_ptr<Plan> plan = get_plan(fs, t, shortcuts, opt.fuse, opt.prologue);
   const uint32_t *dclass = nullptr;
   if (shortcuts && t >= 5) {
     dclass = device_class_table(fs, dev, t, &e);
@@ -419,7 +447,9 @@ int decode_group(const Group &g, cudaStream_t s, const Opts &opt) {
   if (prof || !use_graph) return run_ops(x, s, prof);
 
   GraphKey key{fs->id, g.nframes, g.llr, g.fv, g.xhat, g.uhat, g.fkind, g.prec, t,
-               (shortcuts ? 1 : 0) | (opt.fuse ? 2 : 0) | (g_pdl.load() ? 4 : 0), s, dev, ws};
+               (shortcuts ? 1 : 0) | (opt.fuse ? 2 : 0) | (g_pdl.load() ? 4 : 0) |
+                   (opt.prologue ? 8 : 0),
+               s, dev, ws};
   cudaGraphExec_t exec = nullptr;
   uint64_t kernels = 0;
   {
@@ -589,7 +619,8 @@ int decode_with_scratch(const polar_frozen_set *fs_c, int nframes, const float *
   if (level_scratch_bytes(fs, nframes, prec, &t) > scratch_bytes) return POLAR_EINVAL;
   const bool shortcuts = g_cfg.shortcuts.load() != 0;
   if (shortcuts && t >= 5 && !dclass) return POLAR_EINVAL;
-  std::shared_ptr<Plan> plan = get_plan(fs, t, shortcuts, g_cfg.fuse.load() != 0);
+  std::shared_ptr<Plan> plan = get_plan(fs, t, shortcuts, g_cfg.fuse.load() != 0,
+                                        g_cfg.prologue.load() != 0);
   Exec x{plan.get(), &g, dmask, scratch, (int)fs->log2n, t, shortcuts && t >= 5 ? dclass : nullptr};
   return run_ops(x, s, false);
 }
@@ -660,6 +691,8 @@ int polar_config_set(const char *key, long value) {
     g_cfg.profile = value;
   } else if (!strcmp(key, "fuse")) {
     g_cfg.fuse = value ? 1 : 0;
+  } else if (!strcmp(key, "prologue")) {
+    g_cfg.prologue = value ? 1 : 0;
   } else if (!strcmp(key, "autotune")) {
     g_cfg.autotune = value ? 1 : 0;
   } else if (!strcmp(key, "int8_target")) {
@@ -688,6 +721,7 @@ int polar_config_get(const char *key, long *value) {
   else if (!strcmp(key, "profile")) *value = g_cfg.profile;
   else if (!strcmp(key, "int8_target")) *value = g_cfg.int8_target;
   else if (!strcmp(key, "fuse")) *value = g_cfg.fuse;
+  else if (!strcmp(key, "prologue")) *value = g_cfg.prologue;
   else if (!strcmp(key, "autotune")) *value = g_cfg.autotune;
   else if (!strcmp(key, "persistent")) *value = g_cfg.persistent;
   else if (!strcmp(key, "persist_log2")) *value = g_cfg.persist_log2;
@@ -880,14 +914,19 @@ int polar_autotune(const polar_frozen_set *fs_c, int nframes, const float *llr_d
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
+  // schedule flags: bit 0 = fused streamed steps, bit 1 = the subtree kernel
+  // takes its parent's step (float32 only; reduced storage keeps that step
+  // streamed, so the flag would change nothing there)
+  const int nflags = prec == POLAR_FP32 ? 4 : 2;
   TuneVal best{ts[0], 1, 1e30};
   for (int t : ts) {
-    for (int fuse = 0; fuse <= 1; ++fuse) {
+    for (int flags = 0; flags < nflags; ++flags) {
       Opts o = current_opts();
       o.plain = false;
       o.profile = false;
       o.subtree_log2 = t;
-      o.fuse = fuse != 0;
+      o.fuse = (flags & 1) != 0;
+      o.prologue = (flags & 2) != 0;
       for (int rep = 0; rep < 2; ++rep) {              // warm: workspace, plan, graph
         rc = decode_group(g, s, o);
         if (rc) break;
@@ -900,7 +939,7 @@ int polar_autotune(const polar_frozen_set *fs_c, int nframes, const float *llr_d
       CK(cudaEventSynchronize(e1));
       float ms = 0.f;
       CK(cudaEventElapsedTime(&ms, e0, e1));
-      if (ms / 3.0 < best.ms) best = TuneVal{t, fuse, ms / 3.0};
+      if (ms / 3.0 < best.ms) best = TuneVal{t, flags, ms / 3.0};
     }
     if (rc) break;
   }
@@ -952,7 +991,7 @@ int polar_tune_load(const char *path) {
                " {\"device\": %d, \"log2n\": %d, \"nframes\": %d, \"fkind\": %d, "
                "\"prec\": %d, \"subtree_log2\": %d, \"fuse\": %d, \"ms\": %lf",
                &k.dev, &k.log2n, &k.nframes, &k.fkind, &k.prec, &v.t, &v.fuse, &v.ms) == 8) {
-      if (v.t < 5 || v.t > 14) continue;
+      if (v.t < 5 || v.t > 14 || v.fuse < 0 || v.fuse > 3) continue;
       g_tune[k] = v;
       ++loaded;
     }

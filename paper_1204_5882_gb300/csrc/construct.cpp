@@ -548,6 +548,34 @@ static void plan_visit(const polar_frozen_set *fs, Plan &p, int k, uint64_t o) {
   plan_visit(fs, p, k - 1, o + h);
 }
 
+// Give each subtree the step that produces its input when that step comes
+// right before it: an f (left child) or g (right child) at level t + 1 is
+// done by the subtree kernel itself while it loads the parent's LLRs
+// (pad = 1 / 2), instead of by a separate launch that writes level t.
+static void plan_prologue(Plan &p) {
+  std::vector<Op> out;
+  out.reserve(p.ops.size());
+  const uint64_t T = uint64_t(1) << p.t;
+  for (size_t i = 0; i < p.ops.size(); ++i) {
+    const Op &a = p.ops[i];
+    if ((a.kind == OP_F || a.kind == OP_G) && a.k == p.t + 1 && i + 1 < p.ops.size()) {
+      const Op &b = p.ops[i + 1];
+      const uint64_t child = a.kind == OP_F ? a.o : a.o + T;
+      if (b.kind == OP_ST && b.o == child) {
+        Op m = b;
+        m.pad = a.kind == OP_F ? 1 : 2;
+        out.push_back(m);
+        if (a.kind == OP_F) p.n_f--;
+        else p.n_g--;
+        ++i;
+        continue;
+      }
+    }
+    out.push_back(a);
+  }
+  p.ops.swap(out);
+}
+
 // Merge each f or g step with the f steps that directly continue it (level
 // by level down the left edge) into one fused chain of at most 7 levels.
 static void plan_fuse(Plan &p) {
@@ -574,15 +602,17 @@ static void plan_fuse(Plan &p) {
   p.ops.swap(out);
 }
 
-std::shared_ptr<Plan> get_plan(polar_frozen_set *fs, int t, bool shortcuts, bool fuse) {
+std::shared_ptr<Plan> get_plan(polar_frozen_set *fs, int t, bool shortcuts, bool fuse,
+                               bool prologue) {
   std::lock_guard<std::mutex> g(fs->mu);
-  auto key = std::make_pair(t, (shortcuts ? 1 : 0) | (fuse ? 2 : 0));
+  auto key = std::make_pair(t, (shortcuts ? 1 : 0) | (fuse ? 2 : 0) | (prologue ? 4 : 0));
   auto it = fs->plans.find(key);
   if (it != fs->plans.end()) return it->second;
   auto p = std::make_shared<Plan>();
   p->t = t;
   p->shortcuts = shortcuts;
   plan_visit(fs, *p, (int)fs->log2n, 0);
+  if (prologue && shortcuts && t >= 5) plan_prologue(*p);   // word-aligned subtrees
   if (fuse) plan_fuse(*p);
   fs->plans[key] = p;
   return p;

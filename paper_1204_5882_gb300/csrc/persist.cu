@@ -38,27 +38,6 @@ __device__ __forceinline__ int upper_class(const PFrame &fr, int k, uint64_t o) 
   return NODE_MIXED;
 }
 
-// Asynchronous global -> shared copies (cp.async): each thread copies and
-// later consumes its own slots, so a step needs no barrier inside its loop
-// and keeps no loads in flight in registers.
-__device__ __forceinline__ void cp16(void *dst, const void *src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(
-                   (uint32_t)__cvta_generic_to_shared(dst)),
-               "l"(src)
-               : "memory");
-}
-__device__ __forceinline__ void cp4(void *dst, const void *src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(
-                   (uint32_t)__cvta_generic_to_shared(dst)),
-               "l"(src)
-               : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
 // One upper step, level k -> k-1 over h = 2^(k-1) outputs (h >= 32):
 //   f (G = false): c[i] = f(a[i], a[i + h]);
 //   g (G = true):  c[i] = g(a[i], a[i + h], bit i of beta), beta = the left
@@ -169,6 +148,7 @@ __device__ void decode_frame(const PFrame &fr, float *lv, unsigned char *smraw, 
   p.w_stride = 0;
   p.t = t;
   p.r = 0;
+  p.pre = 0;
   // level k (t <= k < n) at lv + 2^k - 2^t; level n is the channel LLRs
   auto level = [&](int k) -> float * {
     return lv + ((uint64_t(1) << k) - (uint64_t(1) << t));

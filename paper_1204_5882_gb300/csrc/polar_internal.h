@@ -44,7 +44,8 @@ struct Op {
   uint8_t kind;
   uint8_t k;
   uint8_t r;   // partial-sum combine levels done after a unit (ST / R0)
-  uint8_t pad;   // OP_CHAIN: 1 = the first step is g
+  uint8_t pad;   // OP_CHAIN: 1 = the first step is g; OP_ST: 1 / 2 = the subtree
+                 // computes its input itself by f / g from level t + 1
   uint64_t o;
 };
 
@@ -86,7 +87,10 @@ int tv_bit_channel_pe(uint32_t log2n, polar_channel ch, double param, int mu,
 int build_frozen_set_tv(uint32_t log2n, polar_channel ch, double param, int mu, double rate,
                         double sum_pe_max, polar_frozen_set **out);
 NodeClass node_class_host(const polar_frozen_set *fs, int k, uint64_t o);
-std::shared_ptr<Plan> get_plan(polar_frozen_set *fs, int t, bool shortcuts, bool fuse);
+// fuse: chain kernels for runs of streamed steps; prologue: the subtree
+// kernel performs the streamed step that produces its input.
+std::shared_ptr<Plan> get_plan(polar_frozen_set *fs, int t, bool shortcuts, bool fuse,
+                               bool prologue);
 const uint32_t *device_mask(polar_frozen_set *fs, int device, cudaError_t *err);
 // Node-class table of every subtree of 2^t leaves (levels 5..t): per subtree
 // class_words(t) words of "rate 0" bits then as many of "rate 1" bits; node
@@ -154,6 +158,8 @@ struct SubtreeArgs {
   uint64_t o;            // first leaf of the subtree
   int t;                 // subtree log2 size
   int r;                 // combine levels after the subtree
+  int pre;               // 0: in is level t; 1 / 2: in is the parent at level t + 1
+                         // and level t is its f / g (g reads the left child's bits)
   int nframes;
   int fkind;
   int prec;

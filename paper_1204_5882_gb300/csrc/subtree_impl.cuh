@@ -22,6 +22,8 @@
 // memory down to single leaves.
 #pragma once
 
+#include <type_traits>
+
 #include "device_common.cuh"
 #include "polar_internal.h"
 
@@ -45,6 +47,8 @@ struct StParams {
   uint64_t o;
   int t;
   int r;
+  int pre;               // 0: in is level t; 1 / 2: in is the parent (level t + 1) and
+                         // level t is its f / g, computed while loading
 };
 
 // g with the partial sum taken from bit j of a word: b + a or b - a (the
@@ -579,9 +583,44 @@ __device__ __forceinline__ void subtree_body(const StParams &p, bool in_is_llr, 
   if (SC && p.cls)
     for (uint32_t i = tid; i < 2 * CW; i += nth) ctab[i] = p.cls[i];
   S *Lt = w.lvl(t);
-  // Level-t LLRs into shared memory with 16-byte loads, eight in flight per
-  // lane (one warp would otherwise wait a memory latency per element).
-  if (in_is_llr) {
+  if (std::is_same<Tin, float>::value && !p.scale && T >= 32) {
+    // float32 storage (the only one the schedule fuses the parent's step
+    // into): the input rows go to shared memory with cp.async, every copy in
+    // flight at once.  pre = 0: level t itself, straight into Lt.
+    // pre = 1 / 2: the parent's 2T values into L[0, 2T) (the lower half is
+    // free -- it holds the levels below t), then level t is formed in place:
+    // its f (left child) or its g with the left child's partial sums from
+    // x_hat (right child) -- the float operations of the streamed step this
+    // replaces.
+    const float *src = reinterpret_cast<const float *>(p.in) + fr * p.in_stride + p.in_o;
+    float *dst = p.pre ? w.L : Lt;
+    const uint32_t n4 = (p.pre ? 2 * T : T) / 4;
+    for (uint32_t i = tid; i < n4; i += nth) cp16(dst + 4 * i, src + 4 * i);
+    cp_commit();
+    cp_wait<0>();
+    w.sync();
+    if (p.pre) {
+      const uint32_t *bw = p.pre == 2 ? p.xhat + fr * p.w_stride + ((p.o - T) >> 5) : nullptr;
+      const float4 *a4 = reinterpret_cast<const float4 *>(w.L);
+      float4 *b4 = reinterpret_cast<float4 *>(Lt);
+      for (uint32_t i = tid; i < T / 4; i += nth) {
+        const float4 a = a4[i], b = b4[i];
+        float4 v;
+        if (p.pre == 1) {
+          v = make_float4(f_st<Tin, FK>(a.x, b.x, 1.0f), f_st<Tin, FK>(a.y, b.y, 1.0f),
+                          f_st<Tin, FK>(a.z, b.z, 1.0f), f_st<Tin, FK>(a.w, b.w, 1.0f));
+        } else {
+          const uint32_t wd = bw[i >> 3];
+          const int j = (int)((i & 7) << 2);
+          v = make_float4(g_bit(a.x, b.x, wd, j), g_bit(a.y, b.y, wd, j + 1),
+                          g_bit(a.z, b.z, wd, j + 2), g_bit(a.w, b.w, wd, j + 3));
+        }
+        b4[i] = v;                                 // element i of level t, in place
+      }
+    }
+  } else if (in_is_llr) {
+    // Level-t LLRs into shared memory with 16-byte loads, eight in flight per
+    // lane (one warp would otherwise wait a memory latency per element).
     const float *src = reinterpret_cast<const float *>(p.in) + fr * p.in_stride + p.in_o;
     if (T >= 4) {
       const float4 *s4 = reinterpret_cast<const float4 *>(src);
@@ -713,8 +752,10 @@ cudaError_t launch_t(const SubtreeArgs &a, cudaStream_t s) {
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
-  StParams p{a.in,   a.in_stride, a.in_is_llr ? a.o : 0, a.cls, a.scale, a.mask, a.fv,
-             a.xhat, a.uhat,      a.w_stride, a.o,     a.t,    a.r};
+  // float input rows are whole frames: the subtree's (or its parent's) offset
+  const uint64_t in_o = !a.in_is_llr ? 0 : a.pre ? (a.o >> (a.t + 1)) << (a.t + 1) : a.o;
+  StParams p{a.in,   a.in_stride, in_o,       a.cls, a.scale, a.mask, a.fv,
+             a.xhat, a.uhat,      a.w_stride, a.o,   a.t,     a.r,    a.pre};
   return counted(launch_k(kern, a.nframes, 32 * NW, smem, s, p, a.in_is_llr), 1);
 }
 

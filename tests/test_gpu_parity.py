@@ -42,7 +42,8 @@ def words_np(t):
 @pytest.fixture(autouse=True)
 def default_config(P):
     saved = {k: P.polar_config_get(k)
-             for k in ("subtree_log2", "shortcuts", "graphs", "plain", "fuse", "pdl")}
+             for k in ("subtree_log2", "shortcuts", "graphs", "plain", "fuse", "pdl",
+                       "prologue")}
     yield
     for k, v in saved.items():
         P.polar_config_set(k, v)
@@ -150,9 +151,13 @@ def test_minsum_bitexact_small(P, n, kind, t):
     check_minsum(P, n, kind, F=2, seed=1000 * n + t + 7, llr_kind="bsc")
 
 
-@pytest.mark.parametrize("mode", ["no_shortcuts", "no_graphs", "plain", "no_fuse", "no_pdl"])
+@pytest.mark.parametrize("mode", ["no_shortcuts", "no_graphs", "plain", "no_fuse", "no_pdl",
+                                  "prologue", "prologue_no_fuse"])
 def test_minsum_bitexact_modes(P, mode):
-    if mode == "no_pdl":
+    if mode.startswith("prologue"):
+        P.polar_config_set("prologue", 1)
+        P.polar_config_set("fuse", 0 if mode.endswith("no_fuse") else 1)
+    elif mode == "no_pdl":
         P.polar_config_set("pdl", 0)
     elif mode == "no_fuse":
         P.polar_config_set("fuse", 0)
@@ -298,6 +303,32 @@ def test_reduced_storage_workload_bitexact(P, prec):
         assert np.array_equal(S.unpack_bits(xh[f], w.N), ox), f
 
 
+@pytest.mark.parametrize("fkind", ["minsum", "exact"])
+def test_subtree_taking_its_parent_step_changes_no_bit(P, fkind):
+    """The subtree kernel computing its input's f / g from level t + 1 gives
+    the same x_hat / u_hat as the separate streamed step (float32)."""
+    rng = np.random.default_rng(41)
+    n, F, N = 16, 6, 1 << 16
+    fz = random_code(rng, n, "polar")
+    fs = P.polar_frozen_set_from_mask(n, S.pack_bits(fz))
+    L = rng.normal(0.5, 2.0, (F, N)).astype(np.float32)
+    fvb = (rng.integers(0, 2, (F, N)) * fz).astype(np.uint8)
+    fvw = np.stack([S.pack_bits(r) for r in fvb])
+    P.polar_config_set("autotune", 0)
+    try:
+        out = {}
+        for t in (9, 13):
+            for pro in (0, 1):
+                P.polar_config_set("subtree_log2", t)
+                P.polar_config_set("prologue", pro)
+                out[(t, pro)] = gpu_decode(P, fs, L, fvw, fkind)
+        for t in (9, 13):
+            assert np.array_equal(out[(t, 0)][0], out[(t, 1)][0])
+            assert np.array_equal(out[(t, 0)][1], out[(t, 1)][1])
+    finally:
+        P.polar_config_set("autotune", 1)
+
+
 def test_autotune_picks_a_schedule_and_keeps_results(P):
     w = S.Workload("tune", "bsc", 0.03, 16, 0.7, 8, 0x5EED + 50)
     fs = P.polar_build_frozen_set(w.log2n, w.channel, w.param, w.rate)
@@ -310,7 +341,7 @@ def test_autotune_picks_a_schedule_and_keeps_results(P):
     xh = torch.zeros_like(xd)
     P.polar_tune_clear()
     t, fuse, ms = P.polar_autotune(fs, w.frames, llr, fv, xh)
-    assert t in (12, 13, 14) and fuse in (0, 1) and ms > 0
+    assert t in (12, 13, 14) and fuse in (0, 1, 2, 3) and ms > 0
     xh2 = torch.zeros_like(xd)
     P.polar_sc_decode_many(fs, w.frames, llr, fv, xh2)       # uses the tuned schedule
     torch.cuda.synchronize()
