@@ -304,7 +304,22 @@ int ring_launch(polar_server *s) {
     }
     ring_collect(s);                        // words written by the launch that ended
   }
-  if (r.out.empty()) return POLAR_OK;
+  if (r.out.empty()) {
+    // idle with no launch running: restart the 32-bit frame counters long
+    // before they could wrap (the kernel compares claimed < published)
+    if (r.published >= (1u << 31)) {
+      cudaError_t e = cudaMemsetAsync(r.head, 0, sizeof(uint32_t), r.stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(r.stream);
+      if (e != cudaSuccess) {
+        polar::set_last_error(cudaGetErrorString(e));
+        return POLAR_ECUDA;
+      }
+      std::memset(r.done, 0, r.R * sizeof(uint32_t));
+      r.published = 0;
+      __atomic_store_n(r.ctl, 0u, __ATOMIC_RELEASE);
+    }
+    return POLAR_OK;
+  }
   if (r.stopping) {                         // the ended launch no longer reads it
     __atomic_store_n(r.ctl + 1, 0u, __ATOMIC_RELEASE);
     r.stopping = false;
