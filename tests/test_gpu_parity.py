@@ -238,22 +238,32 @@ def test_workload_biawgn_2_24_sampled(P):
 # ------------------------------------------------------------------ exact f, statistics
 def test_exact_f_fer_matches_float64_oracle(P):
     """Exact-f FP32 on the GPU vs exact-f FP64 oracle on the same frames:
-    FERs within two binomial standard errors (BI-AWGN sigma^2 = 1, N = 2^12,
-    rate chosen so that the FER sits mid-range)."""
+    FERs within two binomial standard errors, and bit error rates within two
+    standard errors of the mean of the per-frame bit error rates (bits of a
+    frame fail together, so frames are the independent samples)
+    (BI-AWGN sigma^2 = 1, N = 2^12, rate chosen so that the FER sits
+    mid-range)."""
     w = S.Workload("fer_biawgn_n12", "biawgn", 1.0, 12, 0.40, 400, 0x5EED + 40)
     fs, x, y, xh, _ = decode_workload_gpu(P, w, 0, w.frames, fkind="exact")
     ofz, _ = O.frozen_set(w.log2n, w.channel, w.param, w.rate)
     g_err = o_err = 0
+    g_ber, o_ber = [], []
     for f in range(w.frames):
         xb = S.unpack_bits(x[f], w.N)
-        g_err += int(not np.array_equal(S.unpack_bits(xh[f], w.N), xb))
+        gx = S.unpack_bits(xh[f], w.N)
+        g_err += int(not np.array_equal(gx, xb))
         _, ox, _ = O.decode_frame(w.channel, w.param, x[f], y[f], ofz, "exact", 64)
         o_err += int(not np.array_equal(ox, xb))
+        g_ber.append(float(np.mean(gx != xb)))
+        o_ber.append(float(np.mean(ox != xb)))
     T = w.frames
     pg, po = g_err / T, o_err / T
     se = math.sqrt(max(pg * (1 - pg), 1.0 / T) / T + max(po * (1 - po), 1.0 / T) / T)
     assert 0.02 < po < 0.98, po
     assert abs(pg - po) <= 2 * se, (pg, po, se)
+    bg, bo = np.mean(g_ber), np.mean(o_ber)
+    se_b = math.sqrt(np.var(g_ber) / T + np.var(o_ber) / T)
+    assert bo > 0 and abs(bg - bo) <= 2 * se_b, (bg, bo, se_b)
 
 
 # ------------------------------------------------------------------ reduced storage
