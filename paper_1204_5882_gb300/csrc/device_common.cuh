@@ -75,16 +75,20 @@ __device__ __forceinline__ float f_minsum(float a, float b) {
 // through phi), evaluated as
 //   sgn(a) sgn(b) [min(A,B) + c(A+B) - c(|A-B|)],  c(d) = ln(1 + e^-d),
 // which never forms atanh(+-1).  c is taken with the SFU exponential and
-// logarithm (absolute error ~1e-7, far below any LLR that decides a bit);
-// the magnitude is clamped at zero because rounding can push it slightly
-// negative for tiny inputs.  Exact f is compared with the float64 oracle
-// statistically (frame error rate), never bit for bit.
+// logarithm (absolute error ~1e-7, far below any LLR that decides a bit).
+// For small inputs the three terms cancel and rounding can leave zero or a
+// negative value where the exact update is tiny but nonzero; the magnitude is
+// then raised to the smallest positive float (zero stays zero when an input
+// is zero).  The result thus always carries the exact update's sign, the
+// product of the input signs, which is what makes the rate-1 shortcut (hard
+// decisions of the node's inputs) agree with the full recursion.  Exact f is
+// compared with the float64 oracle statistically (frame error rate).
 __device__ __forceinline__ float corr_c(float d) { return __logf(1.0f + __expf(-d)); }
 
 __device__ __forceinline__ float f_exact(float a, float b) {
   float A = fabsf(a), B = fabsf(b);
   float m = fminf(A, B) + corr_c(A + B) - corr_c(fabsf(A - B));
-  m = fmaxf(m, 0.0f);
+  m = fmaxf(m, fminf(A, B) > 0.0f ? __uint_as_float(1u) : 0.0f);
   uint32_t s = (__float_as_uint(a) ^ __float_as_uint(b)) & 0x80000000u;
   return __uint_as_float(__float_as_uint(m) | s);
 }
@@ -155,10 +159,12 @@ __device__ __forceinline__ float f_st(float a, float b, float s) {
 
 // f on values that may carry a per-frame scale s (int8 storage: values are
 // L * s; s = 1 otherwise): min-sum commutes with the scale, exact f is taken
-// on L.  With s = 1 both are bit-identical to f_op.
+// on L.  With s = 1 both are bit-identical to f_op (a / 1 and 1 * x are exact,
+// so that case skips the divisions: s is uniform across the frame).
 template <int FK>
 __device__ __forceinline__ float f_scaled(float a, float b, float s) {
   if (FK == 0) return f_minsum(a, b);
+  if (s == 1.0f) return f_exact(a, b);
   return s * f_exact(a / s, b / s);
 }
 

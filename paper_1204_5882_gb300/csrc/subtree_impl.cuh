@@ -9,10 +9,11 @@
 //   rate 0 (all frozen): beta = fv F^{(x)k} -- SC decides every leaf from fv
 //                        and beta is the transform of the decisions;
 //   rate 1 (all info):   beta = hard(L) when no input LLR is +-0 -- by
-//                        induction f(a, b) has the sign product and g then
-//                        reproduces sgn(b), so each leaf's decision is the
-//                        hard decision of its input; a zero input falls back
-//                        to the full recursion.
+//                        induction f(a, b) is nonzero with the sign product
+//                        (both f forms keep a nonzero magnitude for nonzero
+//                        inputs) and g then reproduces sgn(b), so each leaf's
+//                        decision is the hard decision of its input; a zero
+//                        input falls back to the full recursion.
 //
 // With shortcuts on, node classes of the levels 5..t come from a table the
 // host precomputes per subtree, and every mixed node of 32 leaves is decoded
@@ -141,6 +142,88 @@ struct Dec<0, FK, CHECK, S> {
 // are uniform words (identical in every lane).  A mixed node of 32 leaves is
 // gathered through shared memory into every lane and decoded by Dec<5>.
 
+// A 16-leaf node whose left child's f values q are already known (the rest
+// of Dec<4>: same operations in the same order).
+template <int FK, typename S>
+__device__ __forceinline__ uint32_t dec16_given_left(const float (&l)[16], const float (&q)[8],
+                                                     uint32_t frz, uint32_t fv, uint32_t &u,
+                                                     float sc) {
+  uint32_t uL, bL;
+  const uint32_t fzL = frz & 0xFFu, fvL = fv & 0xFFu;
+  if (fzL == 0xFFu) {              // rate-0 left child
+    uL = fvL;
+    bL = encode_word(fvL, 3);
+  } else {
+    bL = Dec<3, FK, true, S>::run(q, fzL, fvL, uL, sc);
+  }
+  float r[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) r[j] = rnd<S>(g_bit(l[j], l[j + 8], bL, j));
+  uint32_t uR;
+  const uint32_t bR = Dec<3, FK, true, S>::run(r, (frz >> 8) & 0xFFu, (fv >> 8) & 0xFFu, uR, sc);
+  u = uL | (uR << 8);
+  return (bL ^ bR) | (bR << 8);
+}
+
+// Mixed 32-leaf node with exact f (whose special-function cost dominates):
+// the f and g values of the two top levels are computed once, lane-parallel
+// (lane j forms value j), and gathered through shared memory; the 8-leaf
+// nodes below run redundantly in every lane like Dec<5>.  Every value is the
+// one Dec<5> forms, by the same operations, so the result is bit-identical.
+// (A variant that runs both halves through one copy of the code, to relieve
+// the instruction cache, measured 16 % slower.)
+template <int FK, typename S>
+__device__ __forceinline__ uint32_t dec32_lanes(float v, uint32_t m, uint32_t fv, uint32_t &u,
+                                                float sc, float *gbuf, int lane) {
+  const float hi = __shfl_down_sync(FULL, v, 16);   // leaf LLR lane + 16 (lanes < 16)
+  float l[16], q[8];
+  // Left 16-leaf child: its 16 f values, then its own left child's 8 f values.
+  float c = rnd<S>(f_scaled<FK>(v, hi, sc));
+  float d = rnd<S>(f_scaled<FK>(c, __shfl_down_sync(FULL, c, 8), sc));
+  if (lane < 16) gbuf[lane] = c;
+  if (lane < 8) gbuf[16 + lane] = d;
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < 16; j += 4) {
+    const float4 x = *reinterpret_cast<const float4 *>(gbuf + j);
+    l[j] = x.x, l[j + 1] = x.y, l[j + 2] = x.z, l[j + 3] = x.w;
+  }
+#pragma unroll
+  for (int j = 0; j < 8; j += 4) {
+    const float4 x = *reinterpret_cast<const float4 *>(gbuf + 16 + j);
+    q[j] = x.x, q[j + 1] = x.y, q[j + 2] = x.z, q[j + 3] = x.w;
+  }
+  uint32_t uL, bL;
+  if ((m & 0xFFFFu) == 0xFFFFu) {                    // rate-0 left child
+    uL = fv & 0xFFFFu;
+    bL = encode_word(uL, 4);
+  } else {
+    bL = dec16_given_left<FK, S>(l, q, m & 0xFFFFu, fv & 0xFFFFu, uL, sc);
+  }
+  // Right child: its 16 g values with the left child's partial sums, then
+  // its left child's 8 f values.
+  c = rnd<S>(g_bit(v, hi, bL, lane));
+  d = rnd<S>(f_scaled<FK>(c, __shfl_down_sync(FULL, c, 8), sc));
+  if (lane < 16) gbuf[32 + lane] = c;
+  if (lane < 8) gbuf[48 + lane] = d;
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < 16; j += 4) {
+    const float4 x = *reinterpret_cast<const float4 *>(gbuf + 32 + j);
+    l[j] = x.x, l[j + 1] = x.y, l[j + 2] = x.z, l[j + 3] = x.w;
+  }
+#pragma unroll
+  for (int j = 0; j < 8; j += 4) {
+    const float4 x = *reinterpret_cast<const float4 *>(gbuf + 48 + j);
+    q[j] = x.x, q[j + 1] = x.y, q[j + 2] = x.z, q[j + 3] = x.w;
+  }
+  __syncwarp();
+  uint32_t uR;
+  const uint32_t bR = dec16_given_left<FK, S>(l, q, m >> 16, fv >> 16, uR, sc);
+  u = uL | (uR << 16);
+  return (bL ^ bR) | (bR << 16);
+}
+
 // Mixed or shortcut 32-leaf node; v = this lane's LLR.  Returns beta in the low
 // word and u_hat in the high word.
 template <int FK, typename S, bool UH>
@@ -150,6 +233,11 @@ __device__ __noinline__ uint64_t tile32(float v, uint32_t m, uint32_t fv, float 
   if (m == 0u && !__any_sync(FULL, v == 0.0f)) {
     const uint32_t b = __ballot_sync(FULL, v < 0.0f);
     return (uint64_t)b | ((uint64_t)(UH ? encode_word(b, 5) : 0u) << 32);
+  }
+  if (FK != 0) {
+    uint32_t u;
+    const uint32_t b = dec32_lanes<FK, S>(v, m, fv, u, sc, gbuf, lane);
+    return (uint64_t)b | ((uint64_t)u << 32);
   }
   gbuf[lane] = v;
   __syncwarp();
@@ -280,7 +368,7 @@ struct Warp {
     return __syncthreads_or(b) != 0;
   }
   float sc;                    // int8 per-frame scale (1 otherwise)
-  float *gbuf;                 // 32 floats: gather buffer of the register tiles
+  float *gbuf;                 // 64 floats: gather buffer of the register tiles
 
   // Node of 2^K leaves (5 <= K <= 9) at leaf o, decoded by a register tile.
   template <int K, int FK, bool UH>
@@ -534,7 +622,7 @@ struct Warp {
 __host__ __device__ inline uint32_t bit_words(int t) {
   const uint32_t W = t >= 5 ? (1u << (t - 5)) : 1u;
   const uint32_t CW = t >= 9 ? (1u << (t - 9)) : 1u;
-  return ((4 * W + 2 * CW + 3u) & ~3u) + 32u;
+  return ((4 * W + 2 * CW + 3u) & ~3u) + 64u;
 }
 
 // Tin: storage of the level-t input (the streamed levels); inside the CTA
@@ -570,7 +658,7 @@ __device__ __forceinline__ void subtree_body(const StParams &p, bool in_is_llr, 
   w.cr0 = ctab;
   w.cr1 = ctab + CW;
   w.L = reinterpret_cast<S *>(w.beta + bit_words(t));
-  w.gbuf = reinterpret_cast<float *>(w.beta + bit_words(t) - 32);
+  w.gbuf = reinterpret_cast<float *>(w.beta + bit_words(t) - 64);
 
   const uint64_t ow = p.o >> 5;
   const uint32_t *fvf = p.fv + fr * p.w_stride + ow;

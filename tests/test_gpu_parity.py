@@ -339,6 +339,41 @@ def test_subtree_taking_its_parent_step_changes_no_bit(P, fkind):
         P.polar_config_set("autotune", 1)
 
 
+@pytest.mark.parametrize("kind", ["polar", "random", "all_info"])
+def test_exact_f_same_bits_on_every_path(P, kind):
+    """Every decoder path forms the same exact-f float32 values: the plain
+    decoder (lane-parallel through shared memory down to single leaves), the
+    register tiles with the 32-leaf decoder (top levels lane-parallel, lower
+    ones redundant in every lane) at several subtree sizes, and the persistent
+    decoder.  x_hat / u_hat agree bit for bit."""
+    rng = np.random.default_rng(67)
+    n, F, N = 15, 4, 1 << 15
+    fz = random_code(rng, n, kind)
+    fs = P.polar_frozen_set_from_mask(n, S.pack_bits(fz))
+    L = rng.normal(0.5, 2.0, (F, N)).astype(np.float32)
+    fvb = (rng.integers(0, 2, (F, N)) * fz).astype(np.uint8)
+    fvw = np.stack([S.pack_bits(r) for r in fvb])
+    P.polar_config_set("autotune", 0)
+    try:
+        P.polar_config_set("plain", 1)
+        P.polar_config_set("subtree_log2", 9)
+        ref = gpu_decode(P, fs, L, fvw, "exact")
+        P.polar_config_set("plain", 0)
+        for t in (5, 9, 13):
+            P.polar_config_set("subtree_log2", t)
+            got = gpu_decode(P, fs, L, fvw, "exact")
+            assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]), t
+    finally:
+        P.polar_config_set("autotune", 1)
+    llr = torch.from_numpy(L).to(DEV)
+    fv = to_dev_words(fvw)
+    xh, uh = torch.full_like(fv, -1), torch.full_like(fv, -1)
+    P.polar_sc_decode_persistent([(fs, llr[f], fv[f], xh[f], uh[f]) for f in range(F)],
+                                 fkind="exact")
+    torch.cuda.synchronize()
+    assert np.array_equal(words_np(xh), ref[0]) and np.array_equal(words_np(uh), ref[1])
+
+
 def test_autotune_picks_a_schedule_and_keeps_results(P):
     w = S.Workload("tune", "bsc", 0.03, 16, 0.7, 8, 0x5EED + 50)
     fs = P.polar_build_frozen_set(w.log2n, w.channel, w.param, w.rate)
