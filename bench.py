@@ -130,6 +130,42 @@ def _oracle_frame(f):
     return time.perf_counter() - t0
 
 
+def _oracle_frame_exact(f):
+    """Bob's side of one frame on the float64 exact-f oracle (the paper's
+    phi update in double precision), timed like _oracle_frame."""
+    import oracle as O
+    w, fz = _W["w"], _W["fz"]
+    x, y = S.frame(w, f)
+    fv = O.reveal(O.unpack(x, w.N), fz)
+    yb = O.unpack(y, w.N) if w.channel == "bsc" else y
+    t0 = time.perf_counter()
+    L = O.llr_bsc(yb, w.param, 64) if w.channel == "bsc" else O.llr_biawgn(yb, w.param, 64)
+    O.sc_decode(L, fz, fv, "exact")
+    return time.perf_counter() - t0
+
+
+def cpu_model():
+    """The host CPU as /proc/cpuinfo names it (model name, else the Arm
+    implementer / part codes), with the core count."""
+    name, impl, part = None, None, None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                k, _, v = line.partition(":")
+                k, v = k.strip(), v.strip()
+                if k == "model name" and name is None:
+                    name = v
+                elif k == "CPU implementer" and impl is None:
+                    impl = v
+                elif k == "CPU part" and part is None:
+                    part = v
+    except OSError:
+        pass
+    if name is None and impl is not None:
+        name = f"Arm implementer {impl}, part {part}"
+    return f"{name or 'unknown'}, {os.cpu_count()} cores"
+
+
 def oracle_pool(w):
     """Spawned worker pool over the host cores, with the oracle's frozen set."""
     import oracle as O
@@ -194,7 +230,7 @@ def run_reference(args):
     pool.close()
     value = statistics.mean(rates)
     mean = statistics.mean(step_s)
-    cpu = {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+    cpu = {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
            "sample": f"{sample} frames of {w.name} per step (float32 min-sum recursive SC, "
                      f"LLR map included), one frame per process at a time; rate = processes x "
                      f"N / mean per-frame time"}
@@ -556,12 +592,17 @@ def run_ours(args):
     if pool is not None:
         sample = cores
         times = oracle_step(pool, w, 0, sample)
+        t64 = pool.map(_oracle_frame_exact, range(sample), chunksize=1)
         pool.close()
         cpu = {"value": oracle_rate(times, cores, N), "unit": UNIT, "cores": cores,
                "kind": "oracle", "single_core": N / statistics.mean(times) / 1e6,
                "sample": f"{sample} frames of {w.name} (float32 min-sum recursive SC with the "
                          f"LLR map), one frame per process; rate = processes x N / mean "
-                         f"per-frame time"}
+                         f"per-frame time",
+               "exact_fp64": {"value": oracle_rate(t64, cores, N), "unit": UNIT,
+                              "single_core": N / statistics.mean(t64) / 1e6,
+                              "sample": f"the same {sample} frames in float64 exact f"},
+               "cpu": cpu_model()}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
