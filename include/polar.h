@@ -50,6 +50,7 @@ typedef enum {
     POLAR_ETIMEDOUT = -4,  /* a bounded device-side wait expired */
     POLAR_EBUSY = -5,      /* admission refused (server) */
     POLAR_ENOTFOUND = -6,  /* unknown ticket or option */
+    POLAR_ECANCELED = -7,  /* request withdrawn before it ran (server) */
     POLAR_PENDING = 1      /* request still running (server poll) */
 } polar_status;
 
@@ -107,6 +108,9 @@ const char *polar_last_error_string(void);
  *                   1 (default) = in one persistent launch
  *                   (polar_sc_decode_persistent) when the batch holds more
  *                   than one such group; 2 = always persistent.
+ * Environment: POLAR_LOG set to anything but "" or "0" (read once) prints
+ * "[polar] ..." diagnostics on stderr -- frozen-set constructions (K, time),
+ * autotune choices, tune-cache files and server launches.
  */
 int polar_config_set(const char *key, long value);
 int polar_config_get(const char *key, long *value);
@@ -405,6 +409,16 @@ int polar_server_poll(polar_server *srv, uint64_t ticket, polar_result *out);
 /* As poll, but blocks up to timeout_ms; ETIMEDOUT if still pending. */
 int polar_server_wait(polar_server *srv, uint64_t ticket, double timeout_ms,
                       polar_result *out);
+
+/* Withdraw a request that is still waiting in the queue (not yet launched on
+ * a slot or published to the persistent ring).  Returns POLAR_OK when it was
+ * withdrawn: nothing of it runs, its output buffers are never written, the
+ * caller may release its buffers at once, and poll / wait then report
+ * POLAR_ECANCELED for the ticket (once, like any result).  POLAR_EBUSY when
+ * it has already been launched or has finished: its result arrives as usual.
+ * POLAR_ENOTFOUND for an unknown or already reported ticket; POLAR_EINVAL
+ * for a NULL server. */
+int polar_server_cancel(polar_server *srv, uint64_t ticket);
 
 /* Counters since creation: requests launched (slots) or published to the
  * ring (persistent), completed, refused with EBUSY, and the scratch bytes

@@ -2,8 +2,11 @@
 // per-stream scratch, the streamed schedule of the SC recursion and its
 // replay as CUDA graphs.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <list>
 #include <tuple>
@@ -627,6 +630,24 @@ int decode_with_scratch(const polar_frozen_set *fs_c, int nframes, const float *
 
 void set_last_error(const char *msg) { g_last_error = msg; }
 
+bool log_on() {
+  static const bool on = [] {
+    const char *v = std::getenv("POLAR_LOG");
+    return v && *v && std::strcmp(v, "0") != 0;
+  }();
+  return on;
+}
+
+void log_msg(const char *fmt, ...) {
+  if (!log_on()) return;
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  std::fprintf(stderr, "[polar] %s\n", buf);
+}
+
 // Eager decode (no graphs, no plain mode) for callers that launch many
 // unrelated small batches, such as the request server.
 int decode_eager(const polar_frozen_set *fs, int nframes, const float *llr, const uint32_t *fv,
@@ -668,6 +689,7 @@ const char *polar_strerror(int status) {
     case POLAR_ETIMEDOUT: return "device wait timed out";
     case POLAR_EBUSY: return "admission refused";
     case POLAR_ENOTFOUND: return "not found";
+    case POLAR_ECANCELED: return "cancelled";
     case POLAR_PENDING: return "pending";
     default: return "unknown status";
   }
@@ -758,19 +780,40 @@ void polar_profile_reset(void) {
   }
 }
 
+namespace {
+// Logs one construction: what was asked, the resulting K and the time taken.
+int logged_build(const char *what, uint32_t log2n, polar_channel ch, double param,
+                 polar_frozen_set **out, int rc, std::chrono::steady_clock::time_point t0) {
+  if (polar::log_on()) {
+    const double s =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    polar::log_msg("frozen set (%s): log2n %u, %s %.6g -> status %d, K %llu, %.3f s", what,
+                   log2n, ch == POLAR_BSC ? "bsc" : "biawgn", param, rc,
+                   rc == POLAR_OK && out && *out ? (unsigned long long)(*out)->K : 0ull, s);
+  }
+  return rc;
+}
+}  // namespace
+
 int polar_build_frozen_set(uint32_t log2n, polar_channel ch, double param, double rate,
                            polar_frozen_set **out) {
-  return build_frozen_set(log2n, ch, param, rate, out);
+  const auto t0 = std::chrono::steady_clock::now();
+  return logged_build("rate", log2n, ch, param, out,
+                      build_frozen_set(log2n, ch, param, rate, out), t0);
 }
 
 int polar_build_frozen_set_sum(uint32_t log2n, polar_channel ch, double param,
                                double sum_pe_max, polar_frozen_set **out) {
-  return build_frozen_set_sum(log2n, ch, param, sum_pe_max, out);
+  const auto t0 = std::chrono::steady_clock::now();
+  return logged_build("sum rule", log2n, ch, param, out,
+                      build_frozen_set_sum(log2n, ch, param, sum_pe_max, out), t0);
 }
 
 int polar_build_frozen_set_tv(uint32_t log2n, polar_channel ch, double param, int mu,
                               double rate, double sum_pe_max, polar_frozen_set **out) {
-  return build_frozen_set_tv(log2n, ch, param, mu, rate, sum_pe_max, out);
+  const auto t0 = std::chrono::steady_clock::now();
+  return logged_build("degraded", log2n, ch, param, out,
+                      build_frozen_set_tv(log2n, ch, param, mu, rate, sum_pe_max, out), t0);
 }
 
 int polar_frozen_set_from_mask(uint32_t log2n, const uint32_t *mask_host,
@@ -952,6 +995,9 @@ int polar_autotune(const polar_frozen_set *fs_c, int nframes, const float *llr_d
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[TuneKey{dev, n, nframes, (int)fkind, (int)prec}] = best;
   }
+  log_msg("autotune: log2n %d, %d frames, fkind %d, prec %d -> t %d, fused %d, subtree takes "
+          "parent step %d, %.3f ms per decode", n, nframes, (int)fkind, (int)prec, best.t,
+          best.fuse & 1, (best.fuse >> 1) & 1, best.ms);
   if (best_t) *best_t = best.t;
   if (best_fuse) *best_fuse = best.fuse;
   if (best_ms) *best_ms = best.ms;
@@ -974,6 +1020,7 @@ int polar_tune_save(const char *path) {
   }
   fprintf(f, "]}\n");
   fclose(f);
+  log_msg("tune cache: saved %zu entries to %s", g_tune.size(), path);
   return POLAR_OK;
 }
 
@@ -997,6 +1044,7 @@ int polar_tune_load(const char *path) {
     }
   }
   fclose(f);
+  log_msg("tune cache: loaded %d entries from %s", loaded, path);
   return loaded > 0 ? POLAR_OK : POLAR_ENOTFOUND;
 }
 

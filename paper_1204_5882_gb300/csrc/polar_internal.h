@@ -225,6 +225,11 @@ int decode_with_scratch(const polar_frozen_set *fs, int nframes, const float *ll
                         size_t scratch_bytes, cudaStream_t s);
 bool shortcuts_enabled();
 void set_last_error(const char *msg);
+// Diagnostics on stderr ("[polar] ..." lines) when the environment variable
+// POLAR_LOG is set to anything but "" or "0" (read once): frozen-set
+// construction, autotune choices, tune-cache files, server launches.
+bool log_on();
+void log_msg(const char *fmt, ...) __attribute__((format(printf, 1, 2)));
 int decode_eager(const polar_frozen_set *fs, int nframes, const float *llr, const uint32_t *fv,
                  uint32_t *xhat, uint32_t *uhat, int fkind, int prec, cudaStream_t s);
 size_t decode_scratch_bytes(const polar_frozen_set *fs, int nframes, int prec);

@@ -342,6 +342,8 @@ int ring_launch(polar_server *s) {
     return POLAR_ECUDA;
   }
   r.running = true;
+  polar::log_msg("server: resident decoder launched, %zu frames outstanding, %u published",
+                 r.out.size(), r.published);
   return POLAR_OK;
 }
 
@@ -447,6 +449,8 @@ int ring_create(polar_server *s) {
     return fail(e);
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e);
   s->ws_total = (size_t)r.grid * r.cta_floats * sizeof(float);
+  polar::log_msg("server: persistent, %d resident CTAs (subtree 2^%d), ring of %u frames, "
+                 "%zu bytes of scratch", r.grid, r.t, r.R, s->ws_total);
   return POLAR_OK;
 }
 
@@ -505,6 +509,8 @@ int polar_server_create(const polar_server_config *cfg, polar_server **out) {
   size_t nth = cfg->threads ? (size_t)cfg->threads : 4;
   if (nth > s->slots.size()) nth = s->slots.size();
   for (size_t i = 0; i < nth; ++i) s->threads.emplace_back(scheduler, s, i, nth);
+  polar::log_msg("server: %zu decode slots, %zu scheduler threads, scratch budget %zu bytes",
+                 s->slots.size(), nth, cfg->mem_budget);
   *out = s;
   return POLAR_OK;
 }
@@ -564,6 +570,25 @@ int polar_server_wait(polar_server *s, uint64_t ticket, double timeout_ms, polar
     if (Clock::now() >= deadline) return POLAR_ETIMEDOUT;
     s->cv_done.wait_until(lk, deadline);
   }
+}
+
+int polar_server_cancel(polar_server *s, uint64_t ticket) {
+  if (!s) return POLAR_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto rec = s->records.find(ticket);
+  if (rec == s->records.end()) return POLAR_ENOTFOUND;
+  if (rec->second.status != POLAR_PENDING) return POLAR_EBUSY;   // finished, not yet reported
+  // The schedulers take requests off the queue under this lock (and copy
+  // them before unlocking), so a request found here has not started.
+  for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+    if (it->ticket != ticket) continue;
+    s->queue.erase(it);
+    rec->second.status = POLAR_ECANCELED;
+    rec->second.t_done = Clock::now();
+    s->cv_done.notify_all();
+    return POLAR_OK;
+  }
+  return POLAR_EBUSY;                                              // launched or published
 }
 
 int polar_server_stats(polar_server *s, uint64_t *launched, uint64_t *completed,

@@ -18,6 +18,7 @@ LIB_PATH = _build.LIB_PATH
 
 POLAR_OK, POLAR_EINVAL, POLAR_ENOMEM, POLAR_ECUDA = 0, -1, -2, -3
 POLAR_ETIMEDOUT, POLAR_EBUSY, POLAR_ENOTFOUND, POLAR_PENDING = -4, -5, -6, 1
+POLAR_ECANCELED = -7
 POLAR_BSC, POLAR_BIAWGN = 0, 1
 POLAR_F_MINSUM, POLAR_F_EXACT = 0, 1
 POLAR_FP32, POLAR_FP16, POLAR_INT8 = 0, 1, 2
@@ -97,6 +98,7 @@ def _load():
         "polar_server_submit": ([P, C.POINTER(Request), C.POINTER(U64)], I),
         "polar_server_poll": ([P, U64, C.POINTER(Result)], I),
         "polar_server_wait": ([P, U64, D, C.POINTER(Result)], I),
+        "polar_server_cancel": ([P, U64], I),
         "polar_server_stats": ([P, C.POINTER(U64), C.POINTER(U64), C.POINTER(U64),
                                 C.POINTER(SZ)], I),
         "polar_server_destroy": ([P], None),
@@ -371,6 +373,15 @@ class Server:
         if rc == POLAR_ENOTFOUND:
             raise PolarError("polar_server_wait", rc)
         return (r.status, r.queue_ms, r.latency_ms)
+
+    def cancel(self, ticket):
+        """True when the request was withdrawn before it ran (poll / wait then
+        report POLAR_ECANCELED), False when it already runs or has finished."""
+        rc = _lib.polar_server_cancel(self.handle, int(ticket))
+        if rc == POLAR_EBUSY:
+            return False
+        _check("polar_server_cancel", rc)
+        return True
 
     def stats(self):
         a, b, c, d = C.c_uint64(), C.c_uint64(), C.c_uint64(), C.c_size_t()

@@ -168,6 +168,8 @@ def test_server_config_rejected_on_host(P):
         assert P.lib().polar_server_create(C.byref(cfg), C.byref(h)) == P.POLAR_EINVAL
     assert P.lib().polar_server_submit(None, None, None) == P.POLAR_EINVAL
     assert P.lib().polar_server_poll(None, 1, None) == P.POLAR_EINVAL
+    assert P.lib().polar_server_cancel(None, 1) == P.POLAR_EINVAL
+    assert P.lib().polar_strerror(P.POLAR_ECANCELED).decode() == "cancelled"
 
 
 def test_tune_table_roundtrip(P, tmp_path):
@@ -187,3 +189,22 @@ def test_tune_table_roundtrip(P, tmp_path):
     assert '"log2n": 24, "nframes": 16, "fkind": 1, "prec": 1, "subtree_log2": 13' in text
     assert not P.polar_tune_load(str(tmp_path / "missing.json"))
     P.polar_tune_clear()
+
+
+def test_log_switch_reports_construction(P):
+    """POLAR_LOG=1 prints one line per frozen-set construction on stderr;
+    unset or 0, the library prints nothing."""
+    import sys
+    code = ("from paper_1204_5882_gb300 import polar as P; "
+            "P.polar_build_frozen_set(10, 'bsc', 0.05, 0.5)")
+    out = {}
+    for val in ("1", "0", None):
+        env = {k: v for k, v in os.environ.items() if k != "POLAR_LOG"}
+        if val is not None:
+            env["POLAR_LOG"] = val
+        r = subprocess.run([sys.executable, "-c", code], env=env, cwd=ROOT,
+                           capture_output=True, text=True, timeout=300)
+        assert r.returncode == 0, r.stderr
+        out[val] = r.stderr
+    assert "[polar] frozen set (rate): log2n 10, bsc 0.05 -> status 0, K 512" in out["1"]
+    assert "[polar]" not in out["0"] and "[polar]" not in out[None]

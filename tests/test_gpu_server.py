@@ -227,3 +227,38 @@ def test_persistent_server_refuses_long_codes_and_huge_requests(P):
     with pytest.raises(P.PolarError) as e:             # scratch of one CTA over budget
         P.Server(max_inflight=4, persistent=True, max_log2n=22, mem_budget=1 << 20)
     assert e.value.status == P.POLAR_ENOMEM
+
+
+# ------------------------------------------------------------------ cancellation
+@pytest.mark.gpu
+@pytest.mark.parametrize("persistent", [False, True])
+def test_cancel_withdraws_only_queued_requests(P, persistent):
+    """A withdrawn request reports ECANCELED and its outputs are never
+    written; a request that already runs or has finished is not withdrawn and
+    completes with the result it has alone.  With one slot, requests queue
+    behind the 2^16 decodes ahead of them, so the last one is still queued
+    when it is cancelled.  (The persistent ring may take requests at once,
+    so there either outcome is possible, and each is checked.)"""
+    reqs = make_requests(P, 8, 21, sizes=(16,))
+    expect = alone_results(P, reqs)
+    srv = P.Server(max_inflight=1, persistent=persistent)
+    tickets, outs = [], []
+    for r in reqs:
+        xh = torch.full_like(r["fv"], -1)
+        torch.cuda.synchronize()
+        tickets.append(srv.submit(r["fs"], r["F"], r["llr"], r["fv"], xh))
+        outs.append(xh)
+    withdrawn = [False] * 4 + [srv.cancel(t) for t in tickets[4:]]
+    if not persistent:
+        assert withdrawn[-1]
+    for i, (t, xh) in enumerate(zip(tickets, outs)):
+        st = srv.wait(t, 60000.0)
+        if withdrawn[i]:
+            assert st[0] == P.POLAR_ECANCELED
+            assert bool(torch.all(xh == -1))
+        else:
+            assert st[0] == P.POLAR_OK
+            assert torch.equal(xh.cpu(), expect[i])
+    with pytest.raises(P.PolarError):
+        srv.cancel(tickets[0])                       # reported, so forgotten
+    srv.close()
