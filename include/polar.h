@@ -51,6 +51,7 @@ typedef enum {
     POLAR_EBUSY = -5,      /* admission refused (server) */
     POLAR_ENOTFOUND = -6,  /* unknown ticket or option */
     POLAR_ECANCELED = -7,  /* request withdrawn before it ran (server) */
+    POLAR_EFAULT = -8,     /* guard mode: a kernel wrote outside its scratch */
     POLAR_PENDING = 1      /* request still running (server poll) */
 } polar_status;
 
@@ -108,11 +109,26 @@ const char *polar_last_error_string(void);
  *                   1 (default) = in one persistent launch
  *                   (polar_sc_decode_persistent) when the batch holds more
  *                   than one such group; 2 = always persistent.
+ *   "guard"         debugging aid, 0 (default) or 1: the library's scratch
+ *                   workspaces carry 64 KB guard zones of a fixed byte
+ *                   pattern before and right after the bytes each decode
+ *                   uses; polar_sc_decode, _many, _batch and _persistent
+ *                   then wait for their stream and check both zones,
+ *                   returning POLAR_EFAULT (the offset in
+ *                   polar_last_error_string) if a kernel wrote outside its
+ *                   scratch.  Off, nothing is added or checked.
  * Environment: POLAR_LOG set to anything but "" or "0" (read once) prints
  * "[polar] ..." diagnostics on stderr -- frozen-set constructions (K, time),
  * autotune choices, tune-cache files and server launches.
  */
 int polar_config_set(const char *key, long value);
+
+/* Guard-mode self-test: overwrite one byte of the trailing guard zone of the
+ * scratch workspace that the last decode on `stream` used (a write inside
+ * the allocation), so that the next checked decode on that stream must
+ * report POLAR_EFAULT.  POLAR_ENOTFOUND if that stream has no guarded
+ * workspace. */
+int polar_debug_spoil_guard(void *stream);
 int polar_config_get(const char *key, long *value);
 
 /* Cumulative number of kernels this library has launched in this process,

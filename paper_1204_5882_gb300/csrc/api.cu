@@ -31,6 +31,7 @@ struct Config {
   std::atomic<long> prologue{0};
   std::atomic<long> autotune{1};
   std::atomic<long> persistent{1};
+  std::atomic<long> guard{0};
 };
 
 // ---------------------------------------------------------------- autotuning
@@ -130,9 +131,20 @@ int cuda_fail(cudaError_t e) {
 bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 // ---------------------------------------------------------------- workspace
+// One scratch workspace per (device, stream), grown on demand.  In guard mode
+// ("guard" = 1, a debugging aid) the allocation carries kGuard bytes of a
+// fixed pattern before the workspace and again right after the bytes the
+// current decode asked for; the synchronous decode entry points check both
+// zones afterwards, so a kernel writing past either end of its scratch is
+// reported as POLAR_EFAULT instead of passing silently.
+constexpr size_t kGuard = 64 * 1024;
+constexpr unsigned char kGuardByte = 0xA5;
 struct Workspace {
-  void *ptr = nullptr;
-  size_t bytes = 0;
+  void *ptr = nullptr;        // workspace (after the leading guard zone, if any)
+  size_t bytes = 0;           // capacity
+  char *base = nullptr;       // allocation
+  bool guarded = false;
+  size_t last_req = 0;        // bytes of the latest request (trailing zone follows them)
 };
 std::mutex g_ws_mu;
 std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
@@ -140,29 +152,74 @@ std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
 int get_workspace(int dev, cudaStream_t s, size_t bytes, void **out) {
   std::lock_guard<std::mutex> g(g_ws_mu);
   Workspace &w = g_ws[{dev, s}];
-  if (w.bytes < bytes) {
+  const bool guard = g_cfg.guard.load() != 0;
+  bool fresh = false;
+  if (w.bytes < bytes || w.guarded != guard) {
+    fresh = true;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     CK(cudaStreamIsCapturing(s, &cs));
     if (cs != cudaStreamCaptureStatusNone) {
       g_last_error = "scratch workspace must grow, but the stream is being captured";
       return POLAR_EINVAL;
     }
-    if (w.ptr) {
+    if (w.base) {
       CK(cudaStreamSynchronize(s));
-      cudaFree(w.ptr);
-      w.ptr = nullptr;
-      w.bytes = 0;
+      cudaFree(w.base);
+      w = Workspace{};
     }
-    cudaError_t e = cudaMalloc(&w.ptr, bytes);
+    const size_t cap = std::max(bytes, w.bytes);
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, cap + (guard ? 2 * kGuard : 0));
     if (e != cudaSuccess) {
       cudaGetLastError();
-      w.ptr = nullptr;
       g_last_error = cudaGetErrorString(e);
       return POLAR_ENOMEM;
     }
-    w.bytes = bytes;
+    w.base = static_cast<char *>(p);
+    w.ptr = w.base + (guard ? kGuard : 0);
+    w.bytes = cap;
+    w.guarded = guard;
+    if (guard) CK(cudaMemsetAsync(w.base, kGuardByte, kGuard, s));
+  }
+  if (w.guarded && (fresh || w.last_req != bytes)) {
+    // the trailing zone follows the bytes this decode uses; it is written
+    // when it moves and otherwise left as the last check found (or restored) it
+    CK(cudaMemsetAsync(static_cast<char *>(w.ptr) + bytes, kGuardByte, kGuard, s));
+    w.last_req = bytes;
   }
   *out = w.ptr;
+  return POLAR_OK;
+}
+
+// Guard mode: wait for the stream, then check both guard zones of its
+// workspace.  POLAR_EFAULT (with the first changed offset in the error text)
+// if a kernel wrote outside its scratch.
+int check_guard(cudaStream_t s) {
+  if (g_cfg.guard.load() == 0) return POLAR_OK;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaStreamSynchronize(s));
+  std::lock_guard<std::mutex> g(g_ws_mu);
+  auto it = g_ws.find({dev, s});
+  if (it == g_ws.end() || !it->second.guarded) return POLAR_OK;
+  const Workspace &w = it->second;
+  std::vector<unsigned char> h(kGuard);
+  const char *zones[2] = {w.base, static_cast<const char *>(w.ptr) + w.last_req};
+  const char *names[2] = {"before", "after"};
+  for (int z = 0; z < 2; ++z) {
+    CK(cudaMemcpy(h.data(), zones[z], kGuard, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < kGuard; ++i) {
+      if (h[i] != kGuardByte) {
+        char msg[160];
+        std::snprintf(msg, sizeof msg,
+                      "guard zone %s the scratch workspace overwritten at byte %zu (of %zu)",
+                      names[z], i, kGuard);
+        g_last_error = msg;
+        CK(cudaMemset(const_cast<char *>(zones[z]), kGuardByte, kGuard));
+        return POLAR_EFAULT;
+      }
+    }
+  }
   return POLAR_OK;
 }
 
@@ -667,7 +724,7 @@ void release_stream_workspace(int dev, cudaStream_t s) {
   std::lock_guard<std::mutex> g(g_ws_mu);
   auto it = g_ws.find({dev, s});
   if (it == g_ws.end()) return;
-  if (it->second.ptr) cudaFree(it->second.ptr);
+  if (it->second.base) cudaFree(it->second.base);
   g_ws.erase(it);
 }
 
@@ -690,6 +747,7 @@ const char *polar_strerror(int status) {
     case POLAR_EBUSY: return "admission refused";
     case POLAR_ENOTFOUND: return "not found";
     case POLAR_ECANCELED: return "cancelled";
+    case POLAR_EFAULT: return "out-of-range write detected (guard mode)";
     case POLAR_PENDING: return "pending";
     default: return "unknown status";
   }
@@ -728,6 +786,8 @@ int polar_config_set(const char *key, long value) {
   } else if (!strcmp(key, "persistent")) {
     if (value < 0 || value > 2) return POLAR_EINVAL;
     g_cfg.persistent = value;
+  } else if (!strcmp(key, "guard")) {
+    g_cfg.guard = value ? 1 : 0;
   } else {
     return POLAR_ENOTFOUND;
   }
@@ -748,6 +808,7 @@ int polar_config_get(const char *key, long *value) {
   else if (!strcmp(key, "persistent")) *value = g_cfg.persistent;
   else if (!strcmp(key, "persist_log2")) *value = g_cfg.persist_log2;
   else if (!strcmp(key, "pdl")) *value = g_pdl.load();
+  else if (!strcmp(key, "guard")) *value = g_cfg.guard;
   else return POLAR_ENOTFOUND;
   return POLAR_OK;
 }
@@ -925,8 +986,9 @@ int polar_sc_decode_many(const polar_frozen_set *fs, int nframes, const float *l
           uhat_dev, (int)fkind, (int)prec};
   int rc = check_group(g);
   if (rc) return rc;
-  return decode_group(g, static_cast<cudaStream_t>(stream),
-                      opts_for(g.fs, g.nframes, g.fkind, g.prec));
+  rc = decode_group(g, static_cast<cudaStream_t>(stream),
+                    opts_for(g.fs, g.nframes, g.fkind, g.prec));
+  return rc ? rc : check_guard(static_cast<cudaStream_t>(stream));
 }
 
 int polar_sc_decode(const polar_frozen_set *fs, const float *llr_dev,
@@ -1076,8 +1138,9 @@ int polar_sc_decode_persistent(int nframes, const polar_frame_desc *frames, pola
                                polar_prec prec, void *stream) {
   int rc = check_frames(nframes, frames, (int)fkind, (int)prec);
   if (rc) return rc;
-  return decode_persistent(nframes, frames, (int)fkind, (int)prec,
-                           static_cast<cudaStream_t>(stream));
+  rc = decode_persistent(nframes, frames, (int)fkind, (int)prec,
+                         static_cast<cudaStream_t>(stream));
+  return rc ? rc : check_guard(static_cast<cudaStream_t>(stream));
 }
 
 int polar_sc_decode_batch(int nframes, const polar_frame_desc *frames, polar_fkind fkind,
@@ -1086,9 +1149,11 @@ int polar_sc_decode_batch(int nframes, const polar_frame_desc *frames, polar_fki
   if (rc) return rc;
   const long pm = g_cfg.persistent.load();
   if (prec == POLAR_FP32 && !g_cfg.plain.load() &&
-      (pm == 2 || (pm == 1 && group_end(nframes, frames, 0) < nframes)))
-    return decode_persistent(nframes, frames, (int)fkind, (int)prec,
-                             static_cast<cudaStream_t>(stream));
+      (pm == 2 || (pm == 1 && group_end(nframes, frames, 0) < nframes))) {
+    rc = decode_persistent(nframes, frames, (int)fkind, (int)prec,
+                           static_cast<cudaStream_t>(stream));
+    return rc ? rc : check_guard(static_cast<cudaStream_t>(stream));
+  }
   int i = 0;
   while (i < nframes) {
     const polar_frame_desc &a = frames[i];
@@ -1098,8 +1163,22 @@ int polar_sc_decode_batch(int nframes, const polar_frame_desc *frames, polar_fki
     int rc = decode_group(g, static_cast<cudaStream_t>(stream),
                           opts_for(g.fs, g.nframes, g.fkind, g.prec));
     if (rc) return rc;
+    rc = check_guard(static_cast<cudaStream_t>(stream));
+    if (rc) return rc;
     i = j;
   }
+  return POLAR_OK;
+}
+
+int polar_debug_spoil_guard(void *stream) {
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> g(g_ws_mu);
+  auto it = g_ws.find({dev, s});
+  if (it == g_ws.end() || !it->second.guarded) return POLAR_ENOTFOUND;
+  char *p = static_cast<char *>(it->second.ptr) + it->second.last_req + 100;
+  CK(cudaMemsetAsync(p, 0, 1, s));   // inside the allocation: the trailing guard zone
   return POLAR_OK;
 }
 

@@ -18,7 +18,7 @@ LIB_PATH = _build.LIB_PATH
 
 POLAR_OK, POLAR_EINVAL, POLAR_ENOMEM, POLAR_ECUDA = 0, -1, -2, -3
 POLAR_ETIMEDOUT, POLAR_EBUSY, POLAR_ENOTFOUND, POLAR_PENDING = -4, -5, -6, 1
-POLAR_ECANCELED = -7
+POLAR_ECANCELED, POLAR_EFAULT = -7, -8
 POLAR_BSC, POLAR_BIAWGN = 0, 1
 POLAR_F_MINSUM, POLAR_F_EXACT = 0, 1
 POLAR_FP32, POLAR_FP16, POLAR_INT8 = 0, 1, 2
@@ -99,6 +99,7 @@ def _load():
         "polar_server_poll": ([P, U64, C.POINTER(Result)], I),
         "polar_server_wait": ([P, U64, D, C.POINTER(Result)], I),
         "polar_server_cancel": ([P, U64], I),
+        "polar_debug_spoil_guard": ([P], I),
         "polar_server_stats": ([P, C.POINTER(U64), C.POINTER(U64), C.POINTER(U64),
                                 C.POINTER(SZ)], I),
         "polar_server_destroy": ([P], None),
@@ -142,6 +143,12 @@ def _stream(stream):
 # ------------------------------------------------------------------ config
 def polar_config_set(key: str, value: int):
     _check("polar_config_set", _lib.polar_config_set(key.encode(), int(value)))
+
+
+def polar_debug_spoil_guard(stream=None):
+    """Guard-mode self-test: spoil the trailing guard zone of the scratch
+    that the last decode on `stream` used."""
+    _check("polar_debug_spoil_guard", _lib.polar_debug_spoil_guard(_stream(stream)))
 
 
 def polar_config_get(key: str) -> int:

@@ -62,6 +62,11 @@ def test_strerror_and_config(P):
         P.polar_config_set("persist_log2", 4)
     with pytest.raises(P.PolarError):
         P.polar_config_set("persistent", 3)
+    assert P.polar_config_get("guard") == 0
+    P.polar_config_set("guard", 1)
+    assert P.polar_config_get("guard") == 1
+    P.polar_config_set("guard", 0)
+    assert P.lib().polar_strerror(P.POLAR_EFAULT).decode().startswith("out-of-range write")
 
 
 def test_argument_errors_are_host_side(P):
