@@ -204,6 +204,16 @@ int polar_frozen_set_query(const polar_frozen_set *fs, uint32_t *log2n,
                            uint64_t *k, uint32_t *mask_host,
                            double *sum_pe_info);
 
+/* Make a frozen set resident on CUDA device `device` ahead of its first
+ * decode: its mask and the node-class tables that the decoders read (the
+ * subtree tables for the current "subtree_log2" and for 12, 13 and 14; for
+ * "persist_log2" also the table of the levels above it).  Decodes and the
+ * server otherwise upload them on first use, which on a code's first frame
+ * costs host time inside that call (for the persistent server: inside
+ * polar_server_submit).  Idempotent; tables stay until
+ * polar_frozen_set_free.  EINVAL: NULL set or bad device; ENOMEM; ECUDA. */
+int polar_frozen_set_upload(const polar_frozen_set *fs, int device);
+
 void polar_frozen_set_free(polar_frozen_set *fs);
 
 /* --------------------------------------------------------- channel LLRs */
@@ -406,7 +416,10 @@ typedef struct {
 /* Start a server (EINVAL: bad config or device; ECUDA: stream creation). */
 int polar_server_create(const polar_server_config *cfg, polar_server **out);
 
-/* Queue a request; *ticket identifies it.  EINVAL: bad request (checked on
+/* Queue a request; *ticket identifies it.  In persistent mode a code's first
+ * request uploads its device tables inside this call (see
+ * polar_frozen_set_upload, which does it ahead of time: uploads made while
+ * the resident decoder runs slow it down).  EINVAL: bad request (checked on
  * the host; persistent mode also refuses codes longer than max_log2n and
  * requests of more frames than half the ring, which holds
  * max(8192, 16 * resident CTAs) frames rounded up to a power of two);

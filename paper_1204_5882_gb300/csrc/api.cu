@@ -687,6 +687,20 @@ int decode_with_scratch(const polar_frozen_set *fs_c, int nframes, const float *
 
 void set_last_error(const char *msg) { g_last_error = msg; }
 
+int prepare_tables(polar_frozen_set *fs, int dev, int t, bool upper) {
+  int prev = 0;
+  CK(cudaGetDevice(&prev));
+  if (prev != dev) CK(cudaSetDevice(dev));
+  const int n = (int)fs->log2n, tt = std::min(n, t);
+  cudaError_t e = cudaSuccess;
+  bool ok = device_mask(fs, dev, &e) != nullptr;
+  if (ok && tt >= 5) ok = device_class_table(fs, dev, tt, &e) != nullptr;
+  if (ok && upper && n > tt) ok = device_upper_class_table(fs, dev, tt, &e) != nullptr;
+  if (prev != dev) cudaSetDevice(prev);
+  if (ok) return POLAR_OK;
+  return e == cudaErrorMemoryAllocation ? POLAR_ENOMEM : cuda_fail(e);
+}
+
 bool log_on() {
   static const bool on = [] {
     const char *v = std::getenv("POLAR_LOG");
@@ -880,6 +894,20 @@ int polar_build_frozen_set_tv(uint32_t log2n, polar_channel ch, double param, in
 int polar_frozen_set_from_mask(uint32_t log2n, const uint32_t *mask_host,
                                polar_frozen_set **out) {
   return frozen_set_from_mask(log2n, mask_host, out);
+}
+
+int polar_frozen_set_upload(const polar_frozen_set *fs_c, int device) {
+  if (!fs_c || device < 0) return POLAR_EINVAL;
+  int count = 0;
+  CK(cudaGetDeviceCount(&count));
+  if (device >= count) return POLAR_EINVAL;
+  polar_frozen_set *fs = const_cast<polar_frozen_set *>(fs_c);
+  const int ts[] = {(int)g_cfg.subtree_log2.load(), 12, 13, 14};
+  for (int t : ts) {
+    const int rc = prepare_tables(fs, device, t, false);
+    if (rc) return rc;
+  }
+  return prepare_tables(fs, device, (int)g_cfg.persist_log2.load(), true);
 }
 
 int polar_frozen_set_query(const polar_frozen_set *fs, uint32_t *log2n, uint64_t *k,

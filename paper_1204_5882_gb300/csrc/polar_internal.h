@@ -215,6 +215,11 @@ struct ServeArgs {
   int S;                   // set by launch_serve
 };
 int serve_ctas_per_sm(int fkind, int t);
+// Make a frozen set resident on `dev` for decodes at subtree size t: its
+// mask, the node-class table of the subtrees (t >= 5) and, with `upper`, the
+// class table of the levels above t that the persistent decoder reads.
+// Switches to `dev` for the uploads and back.  OK, ENOMEM or ECUDA.
+int prepare_tables(polar_frozen_set *fs, int dev, int t, bool upper);
 cudaError_t launch_serve(int fkind, ServeArgs a, int t, int grid, cudaStream_t s);
 
 // api.cu: decoding with caller-provided device mask and level scratch.

@@ -522,6 +522,12 @@ int polar_server_submit(polar_server *s, const polar_request *req, uint64_t *tic
   if (s->cfg.persistent) {
     const int nmax = s->cfg.max_log2n ? s->cfg.max_log2n : 22;
     if ((int)req->fs->log2n > nmax || (uint32_t)req->nframes > s->pr.R / 2) return POLAR_EINVAL;
+    // A code's first request uploads its tables here, on the caller's
+    // thread, rather than in the scheduler, where it would hold up the
+    // publication of every other frame.
+    rc = polar::prepare_tables(const_cast<polar_frozen_set *>(req->fs), s->cfg.device, s->pr.t,
+                               true);
+    if (rc) return rc;
   }
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->stop) return POLAR_EINVAL;

@@ -100,6 +100,7 @@ def _load():
         "polar_server_wait": ([P, U64, D, C.POINTER(Result)], I),
         "polar_server_cancel": ([P, U64], I),
         "polar_debug_spoil_guard": ([P], I),
+        "polar_frozen_set_upload": ([P, I], I),
         "polar_server_stats": ([P, C.POINTER(U64), C.POINTER(U64), C.POINTER(U64),
                                 C.POINTER(SZ)], I),
         "polar_server_destroy": ([P], None),
@@ -143,6 +144,11 @@ def _stream(stream):
 # ------------------------------------------------------------------ config
 def polar_config_set(key: str, value: int):
     _check("polar_config_set", _lib.polar_config_set(key.encode(), int(value)))
+
+
+def polar_frozen_set_upload(fs, device=0):
+    """Make the frozen set resident on `device` (mask and class tables)."""
+    _check("polar_frozen_set_upload", _lib.polar_frozen_set_upload(fs.handle, int(device)))
 
 
 def polar_debug_spoil_guard(stream=None):

@@ -174,6 +174,9 @@ def test_server_config_rejected_on_host(P):
     assert P.lib().polar_server_submit(None, None, None) == P.POLAR_EINVAL
     assert P.lib().polar_server_poll(None, 1, None) == P.POLAR_EINVAL
     assert P.lib().polar_server_cancel(None, 1) == P.POLAR_EINVAL
+    assert P.lib().polar_frozen_set_upload(None, 0) == P.POLAR_EINVAL
+    fs = P.polar_build_frozen_set(10, "bsc", 0.05, 0.5)
+    assert P.lib().polar_frozen_set_upload(fs.handle, -1) == P.POLAR_EINVAL
     assert P.lib().polar_strerror(P.POLAR_ECANCELED).decode() == "cancelled"
 
 

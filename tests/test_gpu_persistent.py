@@ -209,3 +209,20 @@ def test_decode_batch_takes_the_persistent_launch(P):
     torch.cuda.synchronize()
     assert P.polar_kernel_launches() - before > 3
     check_against_oracle(frames, inputs)
+
+
+def test_upload_makes_a_code_resident_before_its_first_decode(P):
+    """polar_frozen_set_upload is idempotent, refuses a device that does not
+    exist, and a decode after it gives the oracle's bits."""
+    P.polar_config_set("persist_log2", 9)
+    rng = np.random.default_rng(77)
+    frames, inputs = make_frames(P, rng, [(14, "polar", "gauss"), (12, "front_frozen", "bsc")],
+                                 uhat_every=1)
+    for fs, *_ in frames:
+        P.polar_frozen_set_upload(fs)
+        P.polar_frozen_set_upload(fs)
+    with pytest.raises(P.PolarError):
+        P.polar_frozen_set_upload(frames[0][0], torch.cuda.device_count())
+    P.polar_sc_decode_persistent(frames)
+    torch.cuda.synchronize()
+    check_against_oracle(frames, inputs)
