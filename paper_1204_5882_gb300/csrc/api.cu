@@ -167,9 +167,8 @@ int get_workspace(int dev, cudaStream_t s, size_t bytes, void **out) {
       cudaFree(w.base);
       w = Workspace{};
     }
-    const size_t cap = std::max(bytes, w.bytes);
     void *p = nullptr;
-    cudaError_t e = cudaMalloc(&p, cap + (guard ? 2 * kGuard : 0));
+    cudaError_t e = cudaMalloc(&p, bytes + (guard ? 2 * kGuard : 0));
     if (e != cudaSuccess) {
       cudaGetLastError();
       g_last_error = cudaGetErrorString(e);
@@ -177,7 +176,7 @@ int get_workspace(int dev, cudaStream_t s, size_t bytes, void **out) {
     }
     w.base = static_cast<char *>(p);
     w.ptr = w.base + (guard ? kGuard : 0);
-    w.bytes = cap;
+    w.bytes = bytes;
     w.guarded = guard;
     if (guard) CK(cudaMemsetAsync(w.base, kGuardByte, kGuard, s));
   }
