@@ -188,6 +188,28 @@ def oracle_pool(w):
     return pool, cores
 
 
+def oracle_sample(w, count):
+    """The oracle on the first `count` frames of workload w, one frame per
+    spawned process, in float32 min-sum and in float64 exact f.  Rates
+    extrapolate the mean per-frame time to one process per frame of the
+    workload, capped at the host's cores."""
+    import oracle as O
+    O.build()
+    fz, _ = O.frozen_set(w.log2n, w.channel, w.param, w.rate)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(count, initializer=_oracle_init, initargs=(w.name, fz.tobytes())) as pool:
+        t32 = pool.map(_oracle_frame, range(count), chunksize=1)
+        t64 = pool.map(_oracle_frame_exact, range(count), chunksize=1)
+    procs = min(os.cpu_count() or 1, w.frames)
+    return {"minsum_fp32": {"value": oracle_rate(t32, procs, w.N), "unit": UNIT,
+                            "single_core": w.N / statistics.mean(t32) / 1e6},
+            "exact_fp64": {"value": oracle_rate(t64, procs, w.N), "unit": UNIT,
+                           "single_core": w.N / statistics.mean(t64) / 1e6},
+            "cores": procs, "kind": "oracle",
+            "sample": f"{count} of the {w.frames} frames of {w.name} decoded, one per process; "
+                      f"rates extrapolate the mean per-frame time to {procs} processes"}
+
+
 def oracle_step(pool, w, first, count):
     """Decode frames first..first+count-1 on the pool; per-frame decode seconds
     (input generation excluded)."""
@@ -559,6 +581,8 @@ def run_ours(args):
     extra_n24 = None
     if rank == 0 and not args.no_n24:
         extra_n24 = measure_n24(args, P, dev)
+        if extra_n24 is not None and not args.no_cpu and world == 1:
+            extra_n24["cpu_oracle"] = oracle_sample(S.WORKLOADS["biawgn_s1_n24"], 4)
 
     if rank != 0:
         if world > 1:
