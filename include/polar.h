@@ -123,7 +123,8 @@ const char *polar_last_error_string(void);
  */
 int polar_config_set(const char *key, long value);
 
-/* Guard-mode self-test: overwrite one byte of the trailing guard zone of the
+/* Debugging aid, no counterpart in the paper.  Guard-mode self-test:
+ * overwrite one byte of the trailing guard zone of the
  * scratch workspace that the last decode on `stream` used (a write inside
  * the allocation), so that the next checked decode on that stream must
  * report POLAR_EFAULT.  POLAR_ENOTFOUND if that stream has no guarded
@@ -204,8 +205,9 @@ int polar_frozen_set_query(const polar_frozen_set *fs, uint32_t *log2n,
                            uint64_t *k, uint32_t *mask_host,
                            double *sum_pe_info);
 
-/* Make a frozen set resident on CUDA device `device` ahead of its first
- * decode: its mask and the node-class tables that the decoders read (the
+/* Make a frozen set (Sec. 3's frozen indices, as built above) resident on
+ * CUDA device `device` ahead of its first SC decode (Sec. 4): its mask and
+ * the node-class tables that the decoders read (the
  * subtree tables for the current "subtree_log2" and for 12, 13 and 14; for
  * "persist_log2" also the table of the levels above it).  Decodes and the
  * server otherwise upload them on first use, which on a code's first frame
@@ -440,7 +442,8 @@ int polar_server_wait(polar_server *srv, uint64_t ticket, double timeout_ms,
                       polar_result *out);
 
 /* Withdraw a request that is still waiting in the queue (not yet launched on
- * a slot or published to the persistent ring).  Returns POLAR_OK when it was
+ * a slot or published to the persistent ring) -- part of the serving layer
+ * around Sec. 4's decoder, which the paper does not have.  Returns POLAR_OK when it was
  * withdrawn: nothing of it runs, its output buffers are never written, the
  * caller may release its buffers at once, and poll / wait then report
  * POLAR_ECANCELED for the ticket (once, like any result).  POLAR_EBUSY when
