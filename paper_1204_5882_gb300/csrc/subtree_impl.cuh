@@ -106,7 +106,15 @@ struct Dec {
         }
       }
     }
-    float l[H];
+    float l[H], gp[H], gm[H];
+    // Both outcomes of the right child's g, formed before the left child's
+    // partial sums are known (b - a is b + (-a) in IEEE arithmetic, as in
+    // g_bit); only a select waits for them.
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+      gp[j] = rnd<S>(a[j + H] + a[j]);
+      gm[j] = rnd<S>(a[j + H] - a[j]);
+    }
     uint32_t uL, bL;
     const uint32_t fzL = frz & MH, fvL = fv & MH;
     if (K >= 3 && fzL == MH) {     // rate-0 left child: its f is never needed
@@ -118,7 +126,7 @@ struct Dec {
       bL = Dec<K - 1, FK, true, S>::run(l, fzL, fvL, uL, sc);
     }
 #pragma unroll
-    for (int j = 0; j < H; ++j) l[j] = rnd<S>(g_bit(a[j], a[j + H], bL, j));
+    for (int j = 0; j < H; ++j) l[j] = ((bL >> j) & 1u) ? gm[j] : gp[j];
     uint32_t uR;
     const uint32_t bR = Dec<K - 1, FK, true, S>::run(l, frz >> H, fv >> H, uR, sc);
     u = uL | (uR << H);
