@@ -74,20 +74,39 @@ __device__ __forceinline__ float f_minsum(float a, float b) {
 // Exact check-node update f = 2 atanh(tanh(a/2) tanh(b/2)) (Sec. 4's update
 // through phi), evaluated as
 //   sgn(a) sgn(b) [min(A,B) + c(A+B) - c(|A-B|)],  c(d) = ln(1 + e^-d),
-// which never forms atanh(+-1).  c is taken with the SFU exponential and
-// logarithm (absolute error ~1e-7, far below any LLR that decides a bit).
-// For small inputs the three terms cancel and rounding can leave zero or a
-// negative value where the exact update is tiny but nonzero; the magnitude is
-// then raised to the smallest positive float (zero stays zero when an input
-// is zero).  The result thus always carries the exact update's sign, the
-// product of the input signs, which is what makes the rate-1 shortcut (hard
-// decisions of the node's inputs) agree with the full recursion.  Exact f is
-// compared with the float64 oracle statistically (frame error rate).
-__device__ __forceinline__ float corr_c(float d) { return __logf(1.0f + __expf(-d)); }
+// which never forms atanh(+-1).  With e^x = 2^(x log2 e) and
+// ln y = ln 2 * log2 y, the two corrections are taken in base 2 on the
+// special-function unit (ex2 / lg2, approximate: absolute error ~1e-7, far
+// below any LLR that decides a bit), their difference first, then one fused
+// multiply-add with ln 2 onto min(A,B).  Every step is an explicit
+// instruction or rounded operation, so the result is the same in every
+// calling context, and an input of +-0 (where the two corrections are the
+// same number) gives exactly +-0.  For small inputs the terms cancel and
+// rounding can leave zero or a negative value where the exact update is tiny
+// but nonzero; the magnitude is then raised to the smallest positive float.
+// The result thus always carries the exact update's sign: the product of the
+// input signs when both are nonzero, +-0 otherwise -- what the rate-1 shortcut
+// and the 2-leaf decision rule rely on.  Exact f is compared with the float64
+// oracle statistically (frame and bit error rates).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+// log2(1 + e^-d), i.e. c(d) / ln 2
+__device__ __forceinline__ float corr_log2(float d) {
+  return lg2_approx(1.0f + ex2_approx(d * -1.4426950408889634f));
+}
 
 __device__ __forceinline__ float f_exact(float a, float b) {
   float A = fabsf(a), B = fabsf(b);
-  float m = fminf(A, B) + corr_c(A + B) - corr_c(fabsf(A - B));
+  const float dl = __fsub_rn(corr_log2(A + B), corr_log2(fabsf(A - B)));
+  float m = __fmaf_rn(dl, 0.69314718055994531f, fminf(A, B));
   m = fmaxf(m, fminf(A, B) > 0.0f ? __uint_as_float(1u) : 0.0f);
   uint32_t s = (__float_as_uint(a) ^ __float_as_uint(b)) & 0x80000000u;
   return __uint_as_float(__float_as_uint(m) | s);

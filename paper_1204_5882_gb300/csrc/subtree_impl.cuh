@@ -134,6 +134,34 @@ struct Dec {
   }
 };
 
+// Two leaves.  The left leaf decides 1 iff f(a, b) < 0, and only that sign
+// is ever used: f's magnitude feeds nothing else.  Both f forms return a
+// nonzero magnitude with the sign product when a and b are nonzero and +-0
+// when either is zero, so the decision is read off the sign bits -- for exact
+// f that skips a whole special-function evaluation per node.  With an int8
+// scale below 1 the scaled floor of exact f can underflow to zero, so scaled
+// frames keep the full evaluation.  Same decisions, same bits.
+template <int FK, bool CHECK, typename S>
+struct Dec<1, FK, CHECK, S> {
+  static __device__ __forceinline__ uint32_t run(const float (&a)[2], uint32_t frz, uint32_t fv,
+                                                 uint32_t &u, float sc) {
+    const float gp = rnd<S>(a[1] + a[0]), gm = rnd<S>(a[1] - a[0]);
+    uint32_t u0;
+    if (frz & 1u) {
+      u0 = fv & 1u;
+    } else if (FK == 0 || sc == 1.0f) {
+      const uint32_t x0 = __float_as_uint(a[0]), x1 = __float_as_uint(a[1]);
+      u0 = ((x0 ^ x1) >> 31) & (uint32_t)((x0 << 1) != 0u) & (uint32_t)((x1 << 1) != 0u);
+    } else {
+      u0 = rnd<S>(f_scaled<FK>(a[0], a[1], sc)) < 0.0f ? 1u : 0u;
+    }
+    const float r = u0 ? gm : gp;
+    const uint32_t u1 = (frz & 2u) ? ((fv >> 1) & 1u) : (r < 0.0f ? 1u : 0u);
+    u = u0 | (u1 << 1);
+    return (u0 ^ u1) | (u1 << 1);
+  }
+};
+
 template <int FK, bool CHECK, typename S>
 struct Dec<0, FK, CHECK, S> {
   static __device__ __forceinline__ uint32_t run(const float (&a)[1], uint32_t frz, uint32_t fv,
