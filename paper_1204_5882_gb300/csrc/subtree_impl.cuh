@@ -17,10 +17,11 @@
 //
 // With shortcuts on, node classes of the levels 5..t come from a table the
 // host precomputes per subtree, and every mixed node of 32 leaves is decoded
-// in registers by a fully unrolled recursion (all lanes run it redundantly;
-// no shuffles, no shared-memory round trips below 32 leaves).  The plain
-// variant (shortcuts off) runs every level lane-parallel through shared
-// memory down to single leaves.
+// in registers by a fully unrolled recursion that all lanes run redundantly
+// (min-sum: no shuffles, no shared-memory round trips below 32 leaves; exact
+// f: the node's top two levels are formed lane-parallel first, see
+// dec32_lanes).  The plain variant (shortcuts off) runs every level
+// lane-parallel through shared memory down to single leaves.
 #pragma once
 
 #include <type_traits>
