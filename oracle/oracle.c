@@ -87,25 +87,44 @@ OR_API void or_llr_biawgn_f64(const double *y, size_t n, double sigma2, double *
 /* which is its own inverse on (0, inf), so                                 */
 /*   f(a, b) = sgn(a) sgn(b) phi(phi(|a|) + phi(|b|))                       */
 /*           = 2 atanh(tanh(a/2) tanh(b/2)).                                */
-/* phi(x) = ln(1 + 2/(e^x - 1)) = log1p(2/expm1(x)) is accurate for both    */
-/* small and large x.  Min-sum replaces phi(phi(A)+phi(B)) by min(A, B).    */
-/* The sign of f is taken as - iff exactly one of a, b is negative          */
-/* (signbit); a zero magnitude gives a zero f, whose sign no decision reads.*/
+/* With A = |a|, B = |b| the same quantity is also                          */
+/*   ln((1 + e^(A+B)) / (e^A + e^B))                                        */
+/*     = min(A,B) + ln(1 + e^-(A+B)) - ln(1 + e^-|A-B|)                     */
+/* (divide numerator and denominator by e^max(A,B)).  The two forms are     */
+/* used where each is accurate:                                             */
+/*   - phi form while min(A,B) < F_SPLIT: phi(x) = log1p(2/expm1(x)) keeps  */
+/*     full relative precision, so a tiny f (about A*B/2) keeps its value   */
+/*     and sign;                                                            */
+/*   - min form once min(A,B) >= F_SPLIT: there phi(A) and phi(B) are both  */
+/*     below 2e^-F_SPLIT and would underflow to 0 for A, B beyond about 709 */
+/*     (double) or 88 (float), turning phi(0) into +inf; the min form is    */
+/*     finite everywhere and its result is at least F_SPLIT - ln 2, so its  */
+/*     rounding error is a few ulp of the result.                           */
+/* Min-sum replaces the magnitude by min(A, B).  The sign of f is taken as  */
+/* - iff exactly one of a, b is negative (signbit); a zero magnitude gives  */
+/* a zero f, whose sign no decision reads.                                  */
 /* ------------------------------------------------------------------------ */
+#define F_SPLIT 16.0
 static double phi64(double x) { return log1p(2.0 / expm1(x)); }
 static float phi32(float x) { return log1pf(2.0f / expm1f(x)); }
 
 OR_API double or_f_exact_f64(double a, double b)
 {
-    double A = fabs(a), B = fabs(b);
-    double m = phi64(phi64(A) + phi64(B));
+    double A = fabs(a), B = fabs(b), m;
+    if (fmin(A, B) < F_SPLIT)
+        m = phi64(phi64(A) + phi64(B));
+    else
+        m = fmin(A, B) + log1p(exp(-(A + B))) - log1p(exp(-fabs(A - B)));
     return (signbit(a) != signbit(b)) ? -m : m;
 }
 
 OR_API float or_f_exact_f32(float a, float b)
 {
-    float A = fabsf(a), B = fabsf(b);
-    float m = phi32(phi32(A) + phi32(B));
+    float A = fabsf(a), B = fabsf(b), m;
+    if (fminf(A, B) < (float)F_SPLIT)
+        m = phi32(phi32(A) + phi32(B));
+    else
+        m = fminf(A, B) + log1pf(expf(-(A + B))) - log1pf(expf(-fabsf(A - B)));
     return (signbit(a) != signbit(b)) ? -m : m;
 }
 
@@ -296,7 +315,9 @@ OR_API void or_bhatt_log_bsc(int n, double p, double *out)
 }
 
 /* phi of the Gaussian approximation, in logs: the Chung-Richardson-Urbanke */
-/* form completed by a small-x piece so that phi(0) = 1 (the two-piece form */
+/* form (IEEE Trans. IT 47(2), 2001) completed by the small-x piece of Ha,  */
+/* Kim and McLaughlin (IEEE Trans. IT 50(11), 2004, rate-compatible        */
+/* puncturing of LDPC codes), so that phi(0) = 1 (the two-piece form       */
 /* has phi(0) = e^0.0218 > 1, a fixed point of the minus step at m = 0.029, */
 /* and then rates the "minus^k plus^j" channels of long codes as reliable): */
 /*   x < 0.867      : phi(x) = exp(0.0564 x^2 - 0.48560 x)                  */

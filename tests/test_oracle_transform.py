@@ -84,6 +84,80 @@ def test_f_limits():
     assert O.f_exact(1e-8, 1e-8) == pytest.approx(0.5e-16, rel=1e-6)
 
 
+def _f_literal(a, b, dps=60):
+    """2 atanh(tanh(a/2) tanh(b/2)) evaluated literally in high precision.
+
+    The working precision grows with the inputs so that tanh(x/2) = 1 - 2e^-x
+    still differs from 1: the literal definition, with no rearrangement."""
+    mpmath = pytest.importorskip("mpmath")
+    big = max(abs(a), abs(b))
+    with mpmath.workdps(int(dps + big / 2.3)):
+        a, b = mpmath.mpf(a), mpmath.mpf(b)
+        return float(2 * mpmath.atanh(mpmath.tanh(a / 2) * mpmath.tanh(b / 2)))
+
+
+@pytest.mark.parametrize("a", [50.0, 700.0, 710.0, 1e4, 1e6])
+def test_f_exact_both_inputs_large(a):
+    """Both inputs large: f(a, a + d) = a - ln(1 + e^-d) up to e^-(2a+d), and
+    finite in both precisions (a form through phi(phi(A) + phi(B)) returns
+    +-inf here once phi underflows)."""
+    for d in (0.0, 0.25, 1.0, 3.0, 12.0, 40.0):
+        want = a - math.log1p(math.exp(-d))
+        for sa, sb in ((1, 1), (-1, 1), (1, -1), (-1, -1)):
+            got = O.f_exact(sa * a, sb * (a + d))
+            assert math.isfinite(got)
+            assert got == pytest.approx(sa * sb * want, rel=1e-12)
+            g32 = O.f_exact(float(np.float32(sa * a)), float(np.float32(sb * (a + d))), 32)
+            assert math.isfinite(g32)
+            assert g32 == pytest.approx(sa * sb * want, rel=1e-6)
+    if a <= 710.0:
+        assert O.f_exact(a, a + 1.0) == pytest.approx(_f_literal(a, a + 1.0), rel=1e-14)
+
+
+def test_f_exact_all_magnitudes_against_literal():
+    """Log-uniform magnitudes from 1e-9 to 1e3, any signs: the double oracle
+    keeps relative precision everywhere (tiny results included), the float
+    oracle is within float rounding."""
+    rng = np.random.default_rng(11)
+    for _ in range(600):
+        a, b = 10.0 ** rng.uniform(-9, 3, 2) * rng.choice([-1.0, 1.0], 2)
+        lit = _f_literal(a, b)
+        assert O.f_exact(a, b) == pytest.approx(lit, rel=1e-13)
+        a32, b32 = float(np.float32(a)), float(np.float32(b))
+        assert O.f_exact(a32, b32, 32) == pytest.approx(_f_literal(a32, b32), rel=2e-5)
+
+
+def test_f_exact_continuous_across_the_form_switch():
+    """Inputs around the magnitude where the evaluation changes form: the
+    literal definition decides, to a few ulp."""
+    for A in np.linspace(15.5, 16.5, 41):
+        for B in (A, A + 0.01, A + 1.0, A + 30.0, 2.0 * A):
+            assert O.f_exact(A, B) == pytest.approx(_f_literal(A, B), rel=4e-16 * 8)
+            a32, b32 = float(np.float32(A)), float(np.float32(B))
+            assert O.f_exact(a32, b32, 32) == pytest.approx(_f_literal(a32, b32), rel=1e-6)
+
+
+@pytest.mark.parametrize("chan,param,n", [("bsc", 0.02, 16), ("biawgn", 1.0, 18)])
+def test_exact_leaf_llrs_finite_on_paper_workloads(chan, param, n):
+    """Exact-f SC on a frame shaped like the paper's workloads: every leaf LLR
+    is finite in both precisions (large |L| are common deep in the tree)."""
+    from paper_1204_5882_gb300 import synth
+    N = 1 << n
+    w = synth.Workload("t", chan, param, n, 0.8 if chan == "bsc" else 0.44, 1, 0x5EED + 40 + n)
+    x, y = synth.frame(w, 0)
+    frozen, _ = O.frozen_set(n, chan, param, w.rate)
+    xb = synth.unpack_bits(x, N)
+    fval = O.reveal(xb, frozen)
+    for prec in (64, 32):
+        if chan == "bsc":
+            L = O.llr_bsc(synth.unpack_bits(y, N), param, prec)
+        else:
+            L = O.llr_biawgn(y, param, prec)
+        _, _, leaf = O.sc_decode(L, frozen, fval, "exact", leaf=True)
+        assert np.isfinite(leaf).all()
+        assert np.abs(leaf).max() > (100.0 if prec == 32 else 800.0)
+
+
 def test_f_minsum_closed_form():
     rng = np.random.default_rng(10)
     for _ in range(500):
