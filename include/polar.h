@@ -463,7 +463,7 @@ void polar_server_destroy(polar_server *srv);
 
 /* ------------------------------------------------- decoding, no allocation */
 
-/* Same decode as polar_sc_decode_many, for callers that cannot allocate
+/* Same decisions as polar_sc_decode_many, for callers that cannot allocate
  * device memory: processes whose device memory is all owned by another
  * framework's fixed-size pool, latency-critical loops that cannot afford the
  * device synchronisation cudaMalloc and cudaFree imply, and long-running
@@ -477,18 +477,27 @@ void polar_server_destroy(polar_server *srv);
  * process exits.  The caller still passes all inputs and outputs.
  *   - The first call on a device looks up the array's device address (with
  *     that device current); make that first call before any stream capture.
- *   - Capacity: the mask (N/8 bytes), the subtree node-class table (N/64
- *     bytes when shortcuts are on), each rounded up to 256, plus
- *     nframes * (N - 2^t) * bytes(prec) of levels must fit, t being the
- *     "subtree_log2" setting (e.g. up to 3 frames of 2^20 or 1 frame of 2^22
- *     in FP32 at t = 13).  Larger requests return POLAR_EINVAL before any
- *     launch, with the sizes in polar_last_error_string().
+ *     Under CUDA's lazy module loading (the default) that lookup is also when
+ *     the array takes its 16 MiB of device memory, so make the first call
+ *     before a memory pool claims the whole device; without room it returns
+ *     POLAR_ENOMEM.
+ *   - Options are read once per call: the subtree size t is the autotuned
+ *     one for this batch shape when polar_autotune has an entry for it (as
+ *     in polar_sc_decode_many), else the "subtree_log2" setting; "shortcuts",
+ *     "fuse" and "prologue" as set.  "graphs" is ignored (launches are eager).
+ *   - Capacity: the mask (N/8 bytes) and, with shortcuts on, the subtree
+ *     node-class table (N/64 bytes), each rounded up to 256 bytes, plus, for
+ *     INT8, nframes * 4 bytes of per-frame scales rounded up to 256, plus
+ *     nframes * (N - 2^t) * bytes(prec) of levels must fit.  At t = 13 with
+ *     shortcuts: up to 3 frames of 2^20 or 1 frame of 2^21 in FP32; 7 frames
+ *     of 2^20 or 1 frame of 2^22 in FP16; 15 frames of 2^20 or 3 frames of
+ *     2^22 in INT8.  Larger requests return POLAR_EINVAL before any launch,
+ *     with the sizes in polar_last_error_string().
  *   - Every call on a device shares the one array and leaves its contents
- *     behind; the mask is rewritten each call and every scratch level is
- *     written before it is read.  Calls whose work overlaps on the GPU (other
- *     streams, other host threads) race on the array: serialise them.
- * Launches are eager (the "graphs" option is ignored); results are identical
- * to polar_sc_decode_many. */
+ *     behind; the mask and class table are rewritten each call, the INT8
+ *     scales are written before they are read, and so is every scratch
+ *     level.  Calls whose work overlaps on the GPU (other streams, other
+ *     host threads) race on the array: serialise them. */
 int polar_sc_decode_many_noalloc(const polar_frozen_set *fs, int nframes,
                                  const float *llr_dev, const uint32_t *frozen_vals_dev,
                                  uint32_t *xhat_dev, uint32_t *uhat_dev,

@@ -661,26 +661,43 @@ size_t level_scratch_bytes(const polar_frozen_set *fs, int nframes, int prec, in
   return workspace_bytes(n, t, nframes, prec);
 }
 
+// Options of a decode that runs in caller-supplied scratch, read once so
+// that the sizing and the launches see the same subtree size and shortcut
+// setting even if another thread changes the configuration in between.  The
+// subtree size is the autotuned one for this batch shape when the tuner has
+// an entry, as in polar_sc_decode_many.
+ScratchOpts scratch_opts(const polar_frozen_set *fs, int nframes, int fkind, int prec) {
+  const Opts o = opts_for(fs, nframes, fkind, prec);
+  ScratchOpts so;
+  so.t = std::min<int>((int)fs->log2n, o.subtree_log2);
+  so.shortcuts = o.shortcuts;
+  so.fuse = o.fuse;
+  so.prologue = o.prologue;
+  return so;
+}
+
+size_t scratch_level_bytes(const polar_frozen_set *fs, int nframes, int prec, int t) {
+  return workspace_bytes((int)fs->log2n, t, nframes, prec);
+}
+
 // One batch decoded with launches only: the caller supplies the device mask
 // and the level scratch, so no device memory is allocated and no graph is
 // built.  Host-side the cached schedule of the frozen set is reused.
-bool shortcuts_enabled() { return g_cfg.shortcuts.load() != 0; }
-
 int decode_with_scratch(const polar_frozen_set *fs_c, int nframes, const float *llr,
                         const uint32_t *fv, uint32_t *xhat, uint32_t *uhat, int fkind, int prec,
-                        const uint32_t *dmask, const uint32_t *dclass, void *scratch,
-                        size_t scratch_bytes, cudaStream_t s) {
+                        const ScratchOpts &o, const uint32_t *dmask, const uint32_t *dclass,
+                        void *scratch, size_t scratch_bytes, cudaStream_t s) {
   polar_frozen_set *fs = const_cast<polar_frozen_set *>(fs_c);
   Group g{fs, nframes, llr, fv, xhat, uhat, fkind, prec};
   int rc = check_group(g);
   if (rc) return rc;
-  int t = 0;
-  if (level_scratch_bytes(fs, nframes, prec, &t) > scratch_bytes) return POLAR_EINVAL;
-  const bool shortcuts = g_cfg.shortcuts.load() != 0;
-  if (shortcuts && t >= 5 && !dclass) return POLAR_EINVAL;
-  std::shared_ptr<Plan> plan = get_plan(fs, t, shortcuts, g_cfg.fuse.load() != 0,
-                                        g_cfg.prologue.load() != 0);
-  Exec x{plan.get(), &g, dmask, scratch, (int)fs->log2n, t, shortcuts && t >= 5 ? dclass : nullptr};
+  const int t = o.t;
+  if (t < 1 || t > (int)fs->log2n) return POLAR_EINVAL;
+  if (scratch_level_bytes(fs, nframes, prec, t) > scratch_bytes) return POLAR_EINVAL;
+  if (o.shortcuts && t >= 5 && !dclass) return POLAR_EINVAL;
+  std::shared_ptr<Plan> plan = get_plan(fs, t, o.shortcuts, o.fuse, o.prologue);
+  Exec x{plan.get(), &g, dmask, scratch, (int)fs->log2n, t,
+         o.shortcuts && t >= 5 ? dclass : nullptr};
   return run_ops(x, s, false);
 }
 

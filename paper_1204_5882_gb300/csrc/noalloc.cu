@@ -7,7 +7,11 @@
 //
 // The level scratch and the device copy of the frozen mask live in one
 // file-scope device array of fixed size.  Every GPU that loads this library
-// holds that array until the process exits.
+// holds that array until the process exits.  With CUDA's lazy module loading
+// (the default) the array is taken from device memory when the first call on
+// a device looks up its address, so that first call should come before a
+// caller's pool claims all of the device's memory; if no room is left then,
+// the call returns POLAR_ENOMEM.
 #include <cstdio>
 #include <mutex>
 
@@ -33,8 +37,10 @@ int static_scratch(int dev, unsigned char **out) {
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_polar_static_scratch);
     if (e != cudaSuccess || !p) {
-      polar::set_last_error(cudaGetErrorString(e));
-      return POLAR_ECUDA;
+      polar::set_last_error(e != cudaSuccess ? cudaGetErrorString(e)
+                                             : "no device address for the static array");
+      cudaGetLastError();                 // reported here; leave no stale error behind
+      return e == cudaErrorMemoryAllocation ? POLAR_ENOMEM : POLAR_ECUDA;
     }
     g_static_ptr[dev] = p;
   }
@@ -54,12 +60,14 @@ extern "C" int polar_sc_decode_many_noalloc(const polar_frozen_set *fs, int nfra
   if (!fs || nframes < 1 || !llr_dev || !frozen_vals_dev || !xhat_dev) return POLAR_EINVAL;
   if (prec != POLAR_FP32 && prec != POLAR_FP16 && prec != POLAR_INT8) return POLAR_EINVAL;
   polar_frozen_set *fsm = const_cast<polar_frozen_set *>(fs);
+  // The options are read once: sizing, class table and launches all use
+  // this snapshot, whatever other threads set meanwhile.
+  const polar::ScratchOpts o = polar::scratch_opts(fs, nframes, (int)fkind, (int)prec);
   const size_t mask_bytes = ((fs->mask.size() * sizeof(uint32_t)) + 255) & ~size_t(255);
-  int t = 0;
-  const size_t level_bytes = polar::level_scratch_bytes(fs, nframes, (int)prec, &t);
+  const size_t level_bytes = polar::scratch_level_bytes(fs, nframes, (int)prec, o.t);
   // node-class table of the subtrees, when the shortcuts use one
   std::shared_ptr<std::vector<uint32_t>> ctab;
-  if (polar::shortcuts_enabled() && t >= 5) ctab = polar::class_table_host(fsm, t);
+  if (o.shortcuts && o.t >= 5) ctab = polar::class_table_host(fsm, o.t);
   const size_t class_bytes =
       ctab ? ((ctab->size() * sizeof(uint32_t)) + 255) & ~size_t(255) : 0;
   const size_t need = mask_bytes + class_bytes + level_bytes;
@@ -95,7 +103,7 @@ extern "C" int polar_sc_decode_many_noalloc(const polar_frozen_set *fs, int nfra
   }
   const size_t head = mask_bytes + class_bytes;
   return polar::decode_with_scratch(
-      fs, nframes, llr_dev, frozen_vals_dev, xhat_dev, uhat_dev, (int)fkind, (int)prec,
+      fs, nframes, llr_dev, frozen_vals_dev, xhat_dev, uhat_dev, (int)fkind, (int)prec, o,
       reinterpret_cast<uint32_t *>(base),
       ctab ? reinterpret_cast<uint32_t *>(base + mask_bytes) : nullptr, base + head,
       POLAR_STATIC_SCRATCH_BYTES - head, s);

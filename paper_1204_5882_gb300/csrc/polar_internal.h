@@ -224,11 +224,19 @@ cudaError_t launch_serve(int fkind, ServeArgs a, int t, int grid, cudaStream_t s
 
 // api.cu: decoding with caller-provided device mask and level scratch.
 size_t level_scratch_bytes(const polar_frozen_set *fs, int nframes, int prec, int *t_out);
+// One read of the decode options for a scratch-supplied decode (subtree size
+// t, autotuned when cached; shortcuts; fused streamed steps; prologue).
+struct ScratchOpts {
+  int t;
+  bool shortcuts, fuse, prologue;
+};
+ScratchOpts scratch_opts(const polar_frozen_set *fs, int nframes, int fkind, int prec);
+// Level scratch (and int8 scales) of nframes frames at subtree size t, bytes.
+size_t scratch_level_bytes(const polar_frozen_set *fs, int nframes, int prec, int t);
 int decode_with_scratch(const polar_frozen_set *fs, int nframes, const float *llr,
                         const uint32_t *fv, uint32_t *xhat, uint32_t *uhat, int fkind, int prec,
-                        const uint32_t *dmask, const uint32_t *dclass, void *scratch,
-                        size_t scratch_bytes, cudaStream_t s);
-bool shortcuts_enabled();
+                        const ScratchOpts &o, const uint32_t *dmask, const uint32_t *dclass,
+                        void *scratch, size_t scratch_bytes, cudaStream_t s);
 void set_last_error(const char *msg);
 // Diagnostics on stderr ("[polar] ..." lines) when the environment variable
 // POLAR_LOG is set to anything but "" or "0" (read once): frozen-set

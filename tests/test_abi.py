@@ -216,3 +216,42 @@ def test_log_switch_reports_construction(P):
         out[val] = r.stderr
     assert "[polar] frozen set (rate): log2n 10, bsc 0.05 -> status 0, K 512" in out["1"]
     assert "[polar]" not in out["0"] and "[polar]" not in out[None]
+
+
+def _noalloc_need(log2n, nframes, prec_bytes, t=13, int8=False):
+    """Bytes the allocation-free decode needs, by the sizing rule its header
+    states: mask N/8 and class table N/64 (shortcuts on), each rounded up to
+    256, INT8 scales 4 per frame rounded up to 256, levels F (N - 2^t) b."""
+    up = lambda v: (v + 255) // 256 * 256  # noqa: E731
+    N = 1 << log2n
+    return (up(N // 8) + up(N // 64) + (up(4 * nframes) if int8 else 0)
+            + nframes * (N - (1 << t)) * prec_bytes)
+
+
+# (log2 N, frames, bytes per stored LLR, int8) -> fits; the header's examples
+# at t = 13 and the next size up of each.
+NOALLOC_EXAMPLES = [
+    ((20, 3, 4, False), True), ((20, 4, 4, False), False),
+    ((21, 1, 4, False), True), ((21, 2, 4, False), False), ((22, 1, 4, False), False),
+    ((20, 7, 2, False), True), ((20, 8, 2, False), False),
+    ((22, 1, 2, False), True), ((22, 2, 2, False), False),
+    ((20, 15, 1, True), True), ((20, 16, 1, True), False),
+    ((22, 3, 1, True), True), ((22, 4, 1, True), False),
+]
+
+
+def test_noalloc_documented_capacities(P):
+    """Every capacity example in the header of the allocation-free decode
+    holds for the array size the library reports, and the header names
+    exactly these examples."""
+    cap = P.polar_static_scratch_bytes()
+    assert cap == 16 << 20
+    for (n, F, b, i8), fits in NOALLOC_EXAMPLES:
+        assert (_noalloc_need(n, F, b, int8=i8) <= cap) == fits, (n, F, b, i8)
+    hdr = open(os.path.join(ROOT, "include", "polar.h")).read()
+    doc = hdr[hdr.index("Capacity: the mask"):hdr.index("Larger requests return POLAR_EINVAL")]
+    doc = " ".join(doc.replace("*", " ").split())
+    for phrase in ("up to 3 frames of 2^20 or 1 frame of 2^21 in FP32",
+                   "7 frames of 2^20 or 1 frame of 2^22 in FP16",
+                   "15 frames of 2^20 or 3 frames of 2^22 in INT8"):
+        assert phrase in doc, phrase
