@@ -91,6 +91,15 @@ const char *polar_last_error_string(void);
  *   "fuse"          1 = each streamed f/g step and the f steps continuing it
  *                   run as one fused column kernel (default); 0 = one launch
  *                   per step.
+ *   "split_log2"    s > t: every node of 2^s leaves (not rate 0) is decoded
+ *                   by one launch of one CTA per frame, which runs the f / g
+ *                   steps of the levels s..t+1 itself (over the frame's rows
+ *                   of the scratch workspace, staged through shared memory)
+ *                   and then its subtrees; the levels above s stay streamed
+ *                   launches.  0 (default) = no such units; 6..27, ignored
+ *                   when s <= t, s >= log2 N or shortcuts are off.  Results
+ *                   do not depend on it (every step is the same operation
+ *                   with the same storage rounding).
  *   "prologue"      1 = with float32 storage, each subtree kernel performs
  *                   the streamed step that produces its input (the f or g
  *                   from level t + 1) while loading, instead of a separate
@@ -324,13 +333,16 @@ int polar_sc_decode_persistent(int nframes, const polar_frame_desc *frames,
  * under each candidate schedule -- subtree sizes t = 12, 13, 14 (float32
  * storage only: with FP16 / INT8 the rounded levels depend on t), fused and
  * unfused streamed steps, and (float32) with or without the subtree kernel
- * taking its parent's step -- and keeps the fastest for the batch shape
- * (device, log2 N, nframes, fkind, prec).  While the "autotune" option is 1
- * (default), later decodes of that shape use it.  Synchronous on `stream`;
- * the batch's outputs are overwritten with valid decodes.  *best_fuse
- * receives the schedule flags (bit 0: fused streamed steps, bit 1: the
- * subtree takes its parent's step).  Any of best_t, best_fuse, best_ms may
- * be NULL.  Decisions do not depend on the schedule (float32). */
+ * taking its parent's step; then, at the best t, node units of 2^s leaves
+ * for s = t+1 .. t+4 (see "split_log2") with fused and unfused steps above
+ * them -- and keeps the fastest for the batch shape (device, log2 N,
+ * nframes, fkind, prec).  While the "autotune" option is 1 (default), later
+ * decodes of that shape use it.  Synchronous on `stream`; the batch's
+ * outputs are overwritten with valid decodes.  *best_fuse receives the
+ * schedule flags (bit 0: fused streamed steps, bit 1: the subtree takes its
+ * parent's step, bits 8..15: the node-unit level s, 0 for none).  Any of
+ * best_t, best_fuse, best_ms may be NULL.  Decisions do not depend on the
+ * schedule (float32); with FP16 / INT8 they depend on t only. */
 int polar_autotune(const polar_frozen_set *fs, int nframes, const float *llr_dev,
                    const uint32_t *frozen_vals_dev, uint32_t *xhat_dev,
                    polar_fkind fkind, polar_prec prec, void *stream, int *best_t,

@@ -32,6 +32,7 @@ struct Config {
   std::atomic<long> autotune{1};
   std::atomic<long> persistent{1};
   std::atomic<long> guard{0};
+  std::atomic<long> split_log2{0};   // level of node units (0: none), see get_plan
 };
 
 // ---------------------------------------------------------------- autotuning
@@ -61,8 +62,8 @@ struct ProfRec {
   double bytes;
 };
 const char *const kKinds[] = {"llr",   "stream_f", "stream_g", "subtree",
-                              "rate0", "chain",    "persist"};
-constexpr int kNumKinds = 7;
+                              "rate0", "chain",    "persist",  "node"};
+constexpr int kNumKinds = 8;
 std::mutex g_prof_mu;
 std::vector<ProfRec> g_prof_pending;
 double g_prof_ms[kNumKinds];
@@ -251,6 +252,7 @@ struct Exec {
   void *ws;
   int n, t;
   const uint32_t *dclass;   // class table (shortcuts, t >= 5) or null
+  const uint32_t *ducls = nullptr;   // upper class table (plans with node units)
 };
 
 // Workspace: [int8 scales, F floats rounded up to 256 B][levels t..n-1].
@@ -371,6 +373,38 @@ int run_ops(const Exec &x, cudaStream_t s, bool prof) {
                         g.nframes, kt, kb, g.xhat, W, op.o, scale, s));
         break;
       }
+      case OP_NODE: {
+        NodeArgs a;
+        a.lv = level_ptr(x, t);
+        a.mask = x.dmask;
+        a.cls = x.dclass;
+        a.ucls = x.ducls;
+        a.scale = scale;
+        a.fv = g.fv;
+        a.xhat = g.xhat;
+        a.uhat = g.uhat;
+        a.w_stride = W;
+        a.o = op.o;
+        a.s = op.k;
+        a.t = t;
+        a.n = n;
+        a.r = op.r;
+        a.nframes = g.nframes;
+        a.fkind = g.fkind;
+        a.prec = g.prec;
+        if (!a.ucls || !a.cls) return POLAR_EINVAL;
+        // per frame: the node's steps (each level read twice -- f and g --
+        // and written once per node below it) and its subtrees' traffic
+        const double S2 = double(uint64_t(1) << op.k), T = double(uint64_t(1) << t);
+        double steps = 0;
+        for (int k = t + 1; k <= op.k; ++k) steps += S2 * sb * 1.5 + (S2 / 2) / 8.0;
+        double cb = 0;
+        for (int m = 0; m < op.r; ++m) cb += 3.0 * double(uint64_t(1) << (op.k + m)) / 8.0;
+        ProfScope ps(prof, 7, F * (steps + S2 / T * (T * sb + T / 8.0 * (g.uhat ? 4 : 3)) + cb),
+                     s);
+        CK(launch_node(a, s));
+        break;
+      }
       case OP_R0: {
         const size_t off = op.o >> 5, nw = size_t(1) << (op.k - 5);
         double cb = 0;
@@ -396,6 +430,7 @@ int current_device(int *dev) {
 struct Opts {
   bool plain, shortcuts, graphs, profile, fuse, prologue;
   int subtree_log2;
+  int split;                 // node-unit level (0: none)
 };
 
 Opts current_opts() {
@@ -407,6 +442,7 @@ Opts current_opts() {
   o.fuse = !o.plain && g_cfg.fuse.load() != 0;
   o.prologue = !o.plain && g_cfg.prologue.load() != 0;
   o.subtree_log2 = (int)g_cfg.subtree_log2.load();
+  o.split = o.plain ? 0 : (int)g_cfg.split_log2.load();
   return o;
 }
 
@@ -422,6 +458,7 @@ Opts opts_for(const polar_frozen_set *fs, int nframes, int fkind, int prec) {
     o.subtree_log2 = it->second.t;
     o.fuse = (it->second.fuse & 1) != 0;
     o.prologue = (it->second.fuse & 2) != 0;
+    o.split = (it->second.fuse >> 8) & 0xFF;
   }
   return o;
 }
@@ -440,11 +477,17 @@ int decode_group(const Group &g, cudaStream_t s, const Opts &opt) {
   cudaError_t e;
   const uint32_t *dmask = device_mask(fs, dev, &e);
   if (!dmask) return e == cudaErrorMemoryAllocation ? POLAR_ENOMEM : cuda_fail(e);
-  std::shared_ptr<Plan> plan = get_plan(fs, t, shortcuts, opt.fuse, opt.prologue);
+  std::shared_ptr<Plan> plan =
+      get_plan(fs, t, shortcuts, opt.fuse, opt.prologue, plain ? 0 : opt.split);
   const uint32_t *dclass = nullptr;
   if (shortcuts && t >= 5) {
     dclass = device_class_table(fs, dev, t, &e);
     if (!dclass) return e == cudaErrorMemoryAllocation ? POLAR_ENOMEM : cuda_fail(e);
+  }
+  const uint32_t *ducls = nullptr;
+  if (plan->n_node > 0) {
+    ducls = device_upper_class_table(fs, dev, t, &e);
+    if (!ducls) return e == cudaErrorMemoryAllocation ? POLAR_ENOMEM : cuda_fail(e);
   }
   const int F = plain ? 1 : g.nframes;
   size_t ws_bytes = workspace_bytes(n, t, F, g.prec);
@@ -463,13 +506,13 @@ int decode_group(const Group &g, cudaStream_t s, const Opts &opt) {
       one.fv = g.fv + (size_t)f * W;
       one.xhat = g.xhat + (size_t)f * W;
       one.uhat = g.uhat ? g.uhat + (size_t)f * W : nullptr;
-      Exec x{plan.get(), &one, dmask, ws, n, t, dclass};
+      Exec x{plan.get(), &one, dmask, ws, n, t, dclass, ducls};
       rc = run_ops(x, s, opt.profile);
       if (rc) return rc;
     }
     return POLAR_OK;
   }
-  Exec x{plan.get(), &g, dmask, ws, n, t, dclass};
+  Exec x{plan.get(), &g, dmask, ws, n, t, dclass, ducls};
   const bool prof = opt.profile;
   bool use_graph = graphs && s != nullptr;
   if (use_graph) {
@@ -507,7 +550,7 @@ int decode_group(const Group &g, cudaStream_t s, const Opts &opt) {
 
   GraphKey key{fs->id, g.nframes, g.llr, g.fv, g.xhat, g.uhat, g.fkind, g.prec, t,
                (shortcuts ? 1 : 0) | (opt.fuse ? 2 : 0) | (g_pdl.load() ? 4 : 0) |
-                   (opt.prologue ? 8 : 0),
+                   (opt.prologue ? 8 : 0) | (plan->split << 8),
                s, dev, ws};
   cudaGraphExec_t exec = nullptr;
   uint64_t kernels = 0;
@@ -818,6 +861,9 @@ int polar_config_set(const char *key, long value) {
     g_cfg.persistent = value;
   } else if (!strcmp(key, "guard")) {
     g_cfg.guard = value ? 1 : 0;
+  } else if (!strcmp(key, "split_log2")) {
+    if (value != 0 && (value < 6 || value > 27)) return POLAR_EINVAL;
+    g_cfg.split_log2 = value;
   } else {
     return POLAR_ENOTFOUND;
   }
@@ -839,6 +885,7 @@ int polar_config_get(const char *key, long *value) {
   else if (!strcmp(key, "persist_log2")) *value = g_cfg.persist_log2;
   else if (!strcmp(key, "pdl")) *value = g_pdl.load();
   else if (!strcmp(key, "guard")) *value = g_cfg.guard;
+  else if (!strcmp(key, "split_log2")) *value = g_cfg.split_log2;
   else return POLAR_ENOTFOUND;
   return POLAR_OK;
 }
@@ -1068,29 +1115,57 @@ int polar_autotune(const polar_frozen_set *fs_c, int nframes, const float *llr_d
   // streamed, so the flag would change nothing there)
   const int nflags = prec == POLAR_FP32 ? 4 : 2;
   TuneVal best{ts[0], 1, 1e30};
+  // Mean device time of one decode with options o (after warm-up decodes that
+  // build the workspace, plan and graph).
+  auto timed = [&](const Opts &o, double *ms_out) -> int {
+    int r = POLAR_OK;
+    for (int rep = 0; rep < 2 && !r; ++rep) r = decode_group(g, s, o);
+    if (r) return r;
+    CK(cudaEventRecord(e0, s));
+    for (int rep = 0; rep < 3 && !r; ++rep) r = decode_group(g, s, o);
+    if (r) return r;
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    *ms_out = ms / 3.0;
+    return POLAR_OK;
+  };
+  auto base_opts = [&](int t) {
+    Opts o = current_opts();
+    o.plain = false;
+    o.profile = false;
+    o.subtree_log2 = t;
+    o.split = 0;
+    return o;
+  };
+  // phase 1: subtree size and streamed-step flags
   for (int t : ts) {
-    for (int flags = 0; flags < nflags; ++flags) {
-      Opts o = current_opts();
-      o.plain = false;
-      o.profile = false;
-      o.subtree_log2 = t;
+    for (int flags = 0; flags < nflags && !rc; ++flags) {
+      Opts o = base_opts(t);
       o.fuse = (flags & 1) != 0;
       o.prologue = (flags & 2) != 0;
-      for (int rep = 0; rep < 2; ++rep) {              // warm: workspace, plan, graph
-        rc = decode_group(g, s, o);
-        if (rc) break;
-      }
-      if (rc) break;
-      CK(cudaEventRecord(e0, s));
-      for (int rep = 0; rep < 3 && !rc; ++rep) rc = decode_group(g, s, o);
-      if (rc) break;
-      CK(cudaEventRecord(e1, s));
-      CK(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      CK(cudaEventElapsedTime(&ms, e0, e1));
-      if (ms / 3.0 < best.ms) best = TuneVal{t, flags, ms / 3.0};
+      double ms = 0;
+      rc = timed(o, &ms);
+      if (!rc && ms < best.ms) best = TuneVal{t, flags, ms};
     }
     if (rc) break;
+  }
+  // phase 2: node units of 2^s leaves at that subtree size (the levels s..t+1
+  // inside one CTA per frame; results are the same bits); bits 8..15 of the
+  // flags carry s
+  if (!rc && g_cfg.shortcuts.load() != 0 && best.t >= 5) {
+    for (int sp = best.t + 1; sp <= std::min(n - 1, best.t + 4) && !rc; ++sp) {
+      for (int fu = 0; fu < 2 && !rc; ++fu) {
+        Opts o = base_opts(best.t);
+        o.fuse = fu != 0;
+        o.prologue = false;
+        o.split = sp;
+        double ms = 0;
+        rc = timed(o, &ms);
+        if (!rc && ms < best.ms) best = TuneVal{best.t, fu | (sp << 8), ms};
+      }
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1102,8 +1177,9 @@ int polar_autotune(const polar_frozen_set *fs_c, int nframes, const float *llr_d
     g_tune[TuneKey{dev, n, nframes, (int)fkind, (int)prec}] = best;
   }
   log_msg("autotune: log2n %d, %d frames, fkind %d, prec %d -> t %d, fused %d, subtree takes "
-          "parent step %d, %.3f ms per decode", n, nframes, (int)fkind, (int)prec, best.t,
-          best.fuse & 1, (best.fuse >> 1) & 1, best.ms);
+          "parent step %d, node units 2^%d, %.3f ms per decode", n, nframes, (int)fkind,
+          (int)prec, best.t, best.fuse & 1, (best.fuse >> 1) & 1, (best.fuse >> 8) & 0xFF,
+          best.ms);
   if (best_t) *best_t = best.t;
   if (best_fuse) *best_fuse = best.fuse;
   if (best_ms) *best_ms = best.ms;

@@ -535,6 +535,11 @@ static void plan_visit(const polar_frozen_set *fs, Plan &p, int k, uint64_t o) {
     p.n_st++;
     return;
   }
+  if (k == p.split) {
+    p.ops.push_back(Op{OP_NODE, (uint8_t)k, (uint8_t)unit_r(k, o), 0, o});
+    p.n_node++;
+    return;
+  }
   uint64_t h = uint64_t(1) << (k - 1);
   if (!rate0(k - 1, o)) {
     p.ops.push_back(Op{OP_F, (uint8_t)k, 0, 0, o});
@@ -603,13 +608,17 @@ static void plan_fuse(Plan &p) {
 }
 
 std::shared_ptr<Plan> get_plan(polar_frozen_set *fs, int t, bool shortcuts, bool fuse,
-                               bool prologue) {
+                               bool prologue, int split) {
   std::lock_guard<std::mutex> g(fs->mu);
-  auto key = std::make_pair(t, (shortcuts ? 1 : 0) | (fuse ? 2 : 0) | (prologue ? 4 : 0));
+  // nodes need the class tables and word-aligned units; none at or above the root
+  if (!shortcuts || t < 5 || split <= t || split >= (int)fs->log2n) split = 0;
+  auto key = std::make_pair(t, (shortcuts ? 1 : 0) | (fuse ? 2 : 0) | (prologue ? 4 : 0) |
+                                   (split << 8));
   auto it = fs->plans.find(key);
   if (it != fs->plans.end()) return it->second;
   auto p = std::make_shared<Plan>();
   p->t = t;
+  p->split = split;
   p->shortcuts = shortcuts;
   plan_visit(fs, *p, (int)fs->log2n, 0);
   if (prologue && shortcuts && t >= 5) plan_prologue(*p);   // word-aligned subtrees

@@ -38,6 +38,7 @@ enum OpKind : uint8_t {
   OP_ST = 2,  // decode the subtree of 2^t leaves at o in one CTA
   OP_R0 = 3,  // rate-0 node of 2^k leaves at o: partial sums = fv F^{(x)k}
   OP_CHAIN = 4,  // fused steps level k -> k - r: first g (pad = 1) or f, then f
+  OP_NODE = 5,   // node of 2^k leaves (k > t) at o decoded by one CTA per frame
 };
 
 struct Op {
@@ -51,9 +52,10 @@ struct Op {
 
 struct Plan {
   int t = 0;
+  int split = 0;          // level of the OP_NODE units (0: none)
   bool shortcuts = true;
   std::vector<Op> ops;
-  int n_st = 0, n_f = 0, n_g = 0, n_r0 = 0, n_chain = 0;
+  int n_st = 0, n_f = 0, n_g = 0, n_r0 = 0, n_chain = 0, n_node = 0;
 };
 
 }  // namespace polar
@@ -88,9 +90,11 @@ int build_frozen_set_tv(uint32_t log2n, polar_channel ch, double param, int mu, 
                         double sum_pe_max, polar_frozen_set **out);
 NodeClass node_class_host(const polar_frozen_set *fs, int k, uint64_t o);
 // fuse: chain kernels for runs of streamed steps; prologue: the subtree
-// kernel performs the streamed step that produces its input.
+// kernel performs the streamed step that produces its input; split > t: every
+// node of 2^split leaves that is not rate 0 is one OP_NODE unit (the levels
+// split .. t + 1 then run inside its CTAs instead of as streamed launches).
 std::shared_ptr<Plan> get_plan(polar_frozen_set *fs, int t, bool shortcuts, bool fuse,
-                               bool prologue);
+                               bool prologue, int split = 0);
 const uint32_t *device_mask(polar_frozen_set *fs, int device, cudaError_t *err);
 // Node-class table of every subtree of 2^t leaves (levels 5..t): per subtree
 // class_words(t) words of "rate 0" bits then as many of "rate 1" bits; node
@@ -166,6 +170,29 @@ struct SubtreeArgs {
   bool shortcuts;
 };
 cudaError_t launch_subtree(const SubtreeArgs &a, cudaStream_t s);
+
+// A node of 2^s leaves (s > t) decoded by one CTA per frame: the levels
+// s .. t + 1 inside the CTA over the frame's workspace rows, then its subtrees
+// (node_impl.cuh).  Bit-identical to the streamed schedule of those levels.
+struct NodeArgs {
+  const void *lv;          // workspace level t (storage prec); level k at nframes (2^k - 2^t)
+  const uint32_t *mask;    // device frozen mask (whole code)
+  const uint32_t *cls;     // subtree class table (whole code) or null (no shortcuts)
+  const uint32_t *ucls;    // upper class table of levels t..n
+  const float *scale;      // per-frame int8 scale (null = 1)
+  const uint32_t *fv;
+  uint32_t *xhat;
+  uint32_t *uhat;
+  size_t w_stride;         // words per frame
+  uint64_t o;              // first leaf of the node
+  int s, t, n;             // node level, subtree level, code level
+  int r;                   // combine levels after the node
+  int nframes;
+  int fkind;
+  int prec;
+};
+cudaError_t launch_node(const NodeArgs &a, cudaStream_t s);
+size_t node_smem_bytes_host(int t);
 
 size_t storage_bytes(int prec);
 

@@ -12,8 +12,11 @@
 //                        induction f(a, b) is nonzero with the sign product
 //                        (both f forms keep a nonzero magnitude for nonzero
 //                        inputs) and g then reproduces sgn(b), so each leaf's
-//                        decision is the hard decision of its input; a zero
-//                        input falls back to the full recursion.
+//                        decision is the hard decision of its input.  With
+//                        zero inputs (frequent for the BSC, where g = c - c)
+//                        nodes of up to 512 leaves take the bit recursion of
+//                        rate1_word / Rate1Words, which gives SC's decisions
+//                        exactly; larger nodes fall back to the recursion.
 //
 // With shortcuts on, node classes of the levels 5..t come from a table the
 // host precomputes per subtree, and every mixed node of 32 leaves is decoded
@@ -82,6 +85,81 @@ __device__ __forceinline__ bool signs_if_nonzero(const float (&a)[1 << K], uint3
   *b = v[0];
   return m[0] > 0.0f;
 }
+
+// SC decisions (beta) of a rate-1 node of 2^K <= 32 leaves from two words of
+// its inputs: H (bit j set iff input j < 0) and Z (bit j set iff input j is
+// +-0).  Both f forms give +-0 exactly when an input is +-0 and otherwise a
+// nonzero value with the sign product; g = b +- a is b when a = +-0, +-a when
+// b = +-0, and a nonzero value with the sign of b when both are nonzero and
+// the left decision is their hard-decision XOR.  By induction over the node:
+//   - every nonzero input keeps its hard decision;
+//   - with the halves (x, y) of the node, the left child sees
+//     ZL = Zx | Zy and HL = Hx ^ Hy, the right child ZR = Zx & Zy and
+//     HR = Hy where y != 0, Hx ^ betaL where y = 0;
+//   - a zero leaf decides 0.
+// So only the zero positions need the recursion, and a node without zero
+// inputs returns H at once.  (Checked against recursive SC on rate-1 codes
+// with dense +-0 inputs, both f forms, in the GPU parity tests.)
+template <int K>
+__device__ __forceinline__ uint32_t rate1_word(uint32_t H, uint32_t Z) {
+  if (Z == 0u) return H;
+  if constexpr (K == 0) {
+    return 0u;
+  } else {
+    constexpr int Hh = 1 << (K - 1);
+    constexpr uint32_t M = (1u << Hh) - 1u;
+    const uint32_t Hx = H & M, Hy = (H >> Hh) & M, Zx = Z & M, Zy = (Z >> Hh) & M;
+    const uint32_t ZL = Zx | Zy;
+    const uint32_t bL = rate1_word<K - 1>((Hx ^ Hy) & ~ZL, ZL);
+    const uint32_t ZR = Zx & Zy;
+    const uint32_t bR = rate1_word<K - 1>(((Hy & ~Zy) | ((Hx ^ bL) & Zy)) & ~ZR, ZR);
+    return (bL ^ bR) | (bR << Hh);
+  }
+}
+
+// The same for a rate-1 node of 2^K leaves, 5 <= K <= 9, held as 2^(K-5)
+// words (word r = leaves 32r .. 32r+31).
+template <int K>
+struct Rate1Words {
+  static constexpr int R = 1 << (K - 5), Hf = R / 2;
+  static __device__ __forceinline__ void run(const uint32_t (&H)[R], const uint32_t (&Z)[R],
+                                             uint32_t (&b)[R]) {
+    uint32_t any = 0u;
+#pragma unroll
+    for (int r = 0; r < R; ++r) any |= Z[r];
+    if (any == 0u) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) b[r] = H[r];
+      return;
+    }
+    uint32_t h[Hf], z[Hf], bL[Hf], bR[Hf];
+#pragma unroll
+    for (int r = 0; r < Hf; ++r) {
+      z[r] = Z[r] | Z[r + Hf];
+      h[r] = (H[r] ^ H[r + Hf]) & ~z[r];
+    }
+    Rate1Words<K - 1>::run(h, z, bL);
+#pragma unroll
+    for (int r = 0; r < Hf; ++r) {
+      z[r] = Z[r] & Z[r + Hf];
+      h[r] = ((H[r + Hf] & ~Z[r + Hf]) | ((H[r] ^ bL[r]) & Z[r + Hf])) & ~z[r];
+    }
+    Rate1Words<K - 1>::run(h, z, bR);
+#pragma unroll
+    for (int r = 0; r < Hf; ++r) {
+      b[r] = bL[r] ^ bR[r];
+      b[r + Hf] = bR[r];
+    }
+  }
+};
+
+template <>
+struct Rate1Words<5> {
+  static __device__ __forceinline__ void run(const uint32_t (&H)[1], const uint32_t (&Z)[1],
+                                             uint32_t (&b)[1]) {
+    b[0] = rate1_word<5>(H[0], Z[0]);
+  }
+};
 
 // SC over a node of 2^K leaves held in registers: returns beta (2^K bits)
 // and u_hat in `u`.  frz / fv are the node's mask and frozen values in the
@@ -267,8 +345,9 @@ template <int FK, typename S, bool UH>
 __device__ __noinline__ uint64_t tile32(float v, uint32_t m, uint32_t fv, float sc, float *gbuf,
                                         int lane) {
   if (m == FULL) return (uint64_t)encode_word(fv, 5) | ((uint64_t)fv << 32);
-  if (m == 0u && !__any_sync(FULL, v == 0.0f)) {
-    const uint32_t b = __ballot_sync(FULL, v < 0.0f);
+  if (m == 0u) {                                    // rate 1, zero inputs included
+    const uint32_t b =
+        rate1_word<5>(__ballot_sync(FULL, v < 0.0f), __ballot_sync(FULL, v == 0.0f));
     return (uint64_t)b | ((uint64_t)(UH ? encode_word(b, 5) : 0u) << 32);
   }
   if (FK != 0) {
@@ -318,24 +397,24 @@ struct Tile {
           if (!(r & hw)) bo[r] ^= bo[r + hw];
       return;
     }
-    if (all0) {                                   // rate 1, unless some input is +-0
-      bool z = false;
+    if (all0) {                                   // rate 1, zero inputs included
+      uint32_t H[R], Z[R];
 #pragma unroll
-      for (int r = 0; r < R; ++r) z |= (v[r] == 0.0f);
-      if (!__any_sync(FULL, z)) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) bo[r] = __ballot_sync(FULL, v[r] < 0.0f);
-        if (UH) {
-#pragma unroll
-          for (int r = 0; r < R; ++r) uo[r] = encode_word(bo[r], 5);
-#pragma unroll
-          for (int hw = 1; hw < R; hw *= 2)
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-              if (!(r & hw)) uo[r] ^= uo[r + hw];
-        }
-        return;
+      for (int r = 0; r < R; ++r) {
+        H[r] = __ballot_sync(FULL, v[r] < 0.0f);
+        Z[r] = __ballot_sync(FULL, v[r] == 0.0f);
       }
+      Rate1Words<K>::run(H, Z, bo);
+      if (UH) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) uo[r] = encode_word(bo[r], 5);
+#pragma unroll
+        for (int hw = 1; hw < R; hw *= 2)
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+            if (!(r & hw)) uo[r] ^= uo[r + hw];
+      }
+      return;
     }
     float c[H];
     uint32_t bL[H], uL[H], bR[H], uR[H];
@@ -781,7 +860,7 @@ __device__ __forceinline__ void subtree_body(const StParams &p, bool in_is_llr, 
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
         const uint32_t i = b + nth * r + tid;
-        if (i < n16) q[r] = s16[i];
+        if (i < n16) q[r] = __ldcg(s16 + i);       // past L1: a node CTA writes level t with st.cg
       }
 #pragma unroll
       for (int r = 0; r < 8; ++r) {

@@ -179,7 +179,8 @@ def polar_profile_reset():
     _lib.polar_profile_reset()
 
 
-PROFILE_KINDS = ("llr", "stream_f", "stream_g", "subtree", "rate0", "chain", "persist")
+PROFILE_KINDS = ("llr", "stream_f", "stream_g", "subtree", "rate0", "chain", "persist",
+                 "node")
 
 
 # ------------------------------------------------------------------ frozen sets

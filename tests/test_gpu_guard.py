@@ -33,7 +33,7 @@ def P():
 
 
 KEYS = ("guard", "subtree_log2", "shortcuts", "graphs", "plain", "fuse", "prologue",
-        "autotune", "persist_log2")
+        "autotune", "persist_log2", "split_log2")
 
 
 @pytest.fixture(autouse=True)
@@ -104,6 +104,9 @@ MODES = {
     "unfused_t9": {"subtree_log2": 9, "fuse": 0},
     "prologue_t9": {"subtree_log2": 9, "prologue": 1},
     "plain": {"plain": 1, "subtree_log2": 9},
+    "nodes_t9_s12": {"subtree_log2": 9, "split_log2": 12},
+    "nodes_t9_s10_unfused": {"subtree_log2": 9, "split_log2": 10, "fuse": 0},
+    "nodes_t13_s14": {"subtree_log2": 13, "split_log2": 14},
 }
 
 

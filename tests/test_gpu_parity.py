@@ -43,7 +43,7 @@ def words_np(t):
 def default_config(P):
     saved = {k: P.polar_config_get(k)
              for k in ("subtree_log2", "shortcuts", "graphs", "plain", "fuse", "pdl",
-                       "prologue")}
+                       "prologue", "split_log2", "autotune")}
     yield
     for k, v in saved.items():
         P.polar_config_set(k, v)
@@ -456,3 +456,61 @@ def test_frame_hash_matches_definition_and_detects_errors(P, n):
     got = [int(v) & (2 ** 64 - 1) for v in out.cpu().numpy()]
     assert got == [_hash_reference(w, key) for w in words]
     assert got[0] == got[1] and got[0] != got[2]
+
+
+# ------------------------------------------------------------------ node units
+@pytest.mark.parametrize("fkind,prec", [("minsum", "fp32"), ("exact", "fp32"),
+                                        ("minsum", "fp16"), ("exact", "fp16"),
+                                        ("minsum", "int8"), ("exact", "int8")])
+def test_node_units_same_bits(P, fkind, prec):
+    """Nodes of 2^s leaves decoded by one CTA per frame (the levels s..t+1
+    inside the CTA) give the same x_hat and u_hat, bit for bit, as the
+    schedule that streams those levels; min-sum float32 also equals the
+    oracle.  Several (N, t, s) shapes and code shapes, fused and unfused
+    steps above s, with and without u_hat."""
+    rng = np.random.default_rng(91)
+    P.polar_config_set("autotune", 0)
+    cases = [(12, 5, 7, "random"), (15, 9, 12, "polar"), (15, 9, 10, "polar"),
+             (16, 13, 15, "polar"), (14, 8, 13, "all_info"), (13, 6, 9, "all_frozen"),
+             (17, 9, 11, "random")]
+    for n, t, sp, kind in cases:
+        N, F = 1 << n, 3
+        fz = random_code(rng, n, kind)
+        fs = P.polar_frozen_set_from_mask(n, S.pack_bits(fz))
+        if kind == "random" and fkind == "minsum":     # BSC-like: many exact ties in g
+            L = (np.float32(2.5) * (1 - 2 * (rng.random((F, N)) < 0.1))).astype(np.float32)
+        else:
+            L = rng.normal(0.5, 2.0, (F, N)).astype(np.float32)
+        fvb = (rng.integers(0, 2, (F, N)) * fz).astype(np.uint8)
+        fvw = np.stack([S.pack_bits(r) for r in fvb])
+        P.polar_config_set("subtree_log2", t)
+        for fuse in (1, 0):
+            P.polar_config_set("fuse", fuse)
+            P.polar_config_set("split_log2", 0)
+            ref = gpu_decode(P, fs, L, fvw, fkind, prec)
+            P.polar_config_set("split_log2", sp)
+            got = gpu_decode(P, fs, L, fvw, fkind, prec)
+            assert np.array_equal(got[0], ref[0]), (n, t, sp, kind, fuse)
+            assert np.array_equal(got[1], ref[1]), (n, t, sp, kind, fuse)
+            got_x, _ = gpu_decode(P, fs, L, fvw, fkind, prec, uhat=False)
+            assert np.array_equal(got_x, ref[0]), (n, t, sp, kind, fuse)
+        if fkind == "minsum" and prec == "fp32":
+            for f in range(F):
+                ou, ox = O.sc_decode(L[f], fz, fvb[f], "minsum")
+                assert np.array_equal(S.unpack_bits(got[0][f], N), ox)
+                assert np.array_equal(S.unpack_bits(got[1][f], N), ou)
+
+
+def test_node_units_on_the_bench_workload(P):
+    """The 2^20 workload (16 of its 64 frames) with node units of 2^17 leaves
+    at t = 14: bit-exact against the oracle's float32 min-sum."""
+    w = S.WORKLOADS["bsc_p03_n20"]
+    P.polar_config_set("autotune", 0)
+    P.polar_config_set("subtree_log2", 14)
+    P.polar_config_set("split_log2", 17)
+    fs, x, y, xh, uh = decode_workload_gpu(P, w, 0, 16)
+    ofz, _ = O.frozen_set(w.log2n, w.channel, w.param, w.rate)
+    for f in range(0, 16, 3):
+        ou, ox, _ = O.decode_frame(w.channel, w.param, x[f], y[f], ofz, "minsum", 32)
+        assert np.array_equal(S.unpack_bits(xh[f], w.N), ox)
+        assert np.array_equal(S.unpack_bits(uh[f], w.N), ou)
