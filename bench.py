@@ -367,24 +367,34 @@ def profile_pass(P, stream, step, flush):
     return prof, prof_mode
 
 
-def leg_rooflines(prof, F, t, timing, sm_count, clock_ghz):
-    """Roofline of the subtree kernel (a sequential chain: ALU-lane peak and
-    ns per leaf) and of the streamed stages (HBM), from a profile pass."""
+def leg_rooflines(prof, F, t, timing, sm_count, clock_ghz, split=0):
+    """Roofline of the sequential decoder -- subtree launches (2^t leaves per
+    frame) and node launches (2^s leaves per frame, their levels s..t+1 run
+    inside the CTA) -- against the ALU-lane peak, with ns per leaf, and of the
+    streamed stages (whole-GPU f / g launches) against HBM, from a profile
+    pass."""
     peaks = measured_peaks()
     hbm = peaks["hbm_gbs"] if peaks else 6800.0
     peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s"
     sub = None
-    ms, n, _ = prof["subtree"]
-    if ms > 0 and n:
-        ops = n * F * t * (1 << t)                  # f/g evaluations of the recursion
+    ms_s, n_s, _ = prof["subtree"]
+    ms_n, n_n, _ = prof.get("node", (0.0, 0, 0.0))
+    if (ms_s > 0 and n_s) or (ms_n > 0 and n_n):
+        ops = n_s * F * t * (1 << t) + (n_n * F * split * (1 << split) if n_n else 0)
+        leaves = n_s * (1 << t) + (n_n * (1 << split) if n_n else 0)
+        ms = ms_s + ms_n
         ach = ops / (ms / 1e3) / 1e12
         alu_peak = sm_count * 128 * clock_ghz / 1e3  # T simple FP32 ops/s
+        kernel = "subtree" if not n_n else ("node" if not n_s else "subtree+node")
+        per = (f"{F} frames x t*2^t = {F * t * (1 << t)} f/g evaluations" if not n_n else
+               f"{F} frames x s*2^s = {F * split * (1 << split)} f/g evaluations per node launch"
+               + (f", {F * t * (1 << t)} per subtree launch" if n_s else ""))
         sub = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "Tops/s",
-               "frac": ach / alu_peak, "traffic": None, "kernel": "subtree",
-               "launches": n, "avg_launch_us": ms / n * 1e3,
-               "work_per_launch": f"{F} frames x t*2^t = {F * t * (1 << t)} f/g evaluations",
+               "frac": ach / alu_peak, "traffic": None, "kernel": kernel,
+               "launches": n_s + n_n, "avg_launch_us": ms / (n_s + n_n) * 1e3,
+               "work_per_launch": per,
                "peak_source": f"{sm_count} SMs x 128 FP32 lanes x {clock_ghz:.2f} GHz",
-               "ns_per_leaf_per_frame": ms * 1e6 / (n * (1 << t)), "timing": timing}
+               "ns_per_leaf_per_frame": ms * 1e6 / leaves, "timing": timing}
     kinds = ["stream_f", "stream_g", "chain"]
     sms = sum(prof[k][0] for k in kinds)
     sby = sum(prof[k][2] for k in kinds)
@@ -397,6 +407,18 @@ def leg_rooflines(prof, F, t, timing, sm_count, clock_ghz):
                     "kernels": kinds, "launches": sn, "avg_launch_us": sms / sn * 1e3,
                     "alg_bytes_per_launch": sby / sn, "timing": timing}
     return sub, streamed
+
+
+def schedule_of(tuned, P=None):
+    """The schedule a decode ran with: the tuned one, else the options."""
+    if tuned:
+        return {"subtree_log2": tuned[0], "fused": bool(tuned[1] & 1),
+                "subtree_takes_parent_step": bool(tuned[1] & 2),
+                "node_log2": (tuned[1] >> 8) & 0xFF, "source": "polar_autotune"}
+    return {"subtree_log2": P.polar_config_get("subtree_log2"),
+            "fused": bool(P.polar_config_get("fuse")),
+            "subtree_takes_parent_step": bool(P.polar_config_get("prologue")),
+            "node_log2": P.polar_config_get("split_log2"), "source": "options"}
 
 
 def decode_leg(P, dev, stream, fs, F, N, llr, fv, xd, fkind, prec, flush, steps=5, warmup=3,
@@ -434,16 +456,16 @@ def decode_leg(P, dev, stream, fs, F, N, llr, fv, xd, fkind, prec, flush, steps=
         ms = sum(ms_list) / steps
         fer = float((xh != xd).any(dim=1).float().mean().item())
         prof, mode = profile_pass(P, stream, step, flush)
-    t = min(int(math.log2(N)), tuned[0] if tuned else P.polar_config_get("subtree_log2"))
+    sched = schedule_of(tuned, P)
+    t = min(int(math.log2(N)), sched["subtree_log2"])
     props = torch.cuda.get_device_properties(dev)
-    sub, streamed = leg_rooflines(prof, F, t, mode, props.multi_processor_count, 2.07)
+    sub, streamed = leg_rooflines(prof, F, t, mode, props.multi_processor_count, 2.07,
+                                  sched["node_log2"])
     return {"value": F * N / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms,
             "steps": steps, "warmup": warmup, "frames": F, "N": N, "fkind": fkind,
             "storage": prec, "fer": fer,
             "dtype": "f32" if prec == "fp32" else f"f32 compute, {prec} storage",
-            "schedule": {"subtree_log2": tuned[0], "fused": bool(tuned[1] & 1),
-                         "subtree_takes_parent_step": bool(tuned[1] & 2)} if tuned
-            else "default",
+            "schedule": sched,
             "roofline": sub, "roofline_streamed": streamed,
             "kernel_time_ms": {k: {"ms": prof[k][0], "launches": prof[k][1]} for k in prof}}
 
@@ -720,40 +742,12 @@ def run_ours(args):
         return
 
     # ---- roofline of the dominant kernel and of the streamed stages
-    peaks = measured_peaks()
-    hbm = peaks["hbm_gbs"] if peaks else 6800.0
-    peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s"
-    dom = max(prof, key=lambda k: prof[k][0])
+    sched = schedule_of(tuned, P)
+    t = min(w.log2n, sched["subtree_log2"])
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     clock_ghz = (ck.get("sm_max_mhz") or 2070.0) / 1e3
-
-    def hbm_roof(kinds):
-        ms = sum(prof[k][0] for k in kinds)
-        by = sum(prof[k][2] for k in kinds)
-        n = sum(prof[k][1] for k in kinds)
-        if ms <= 0 or n == 0:
-            return None
-        ach = by / (ms / 1e3) / 1e9
-        return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": None, "peak_source": peak_src,
-                "kernels": list(kinds), "launches": n, "avg_launch_us": ms / n * 1e3,
-                "alg_bytes_per_launch": by / n, "timing": prof_mode}
-
-    if dom == "subtree":
-        ms, n, _ = prof["subtree"]
-        t = min(w.log2n, tuned[0] if tuned else (args.subtree_log2 or
-                                                 P.polar_config_get("subtree_log2")))
-        ops = n * F * t * (1 << t)                  # f/g evaluations of the recursion
-        ach = ops / (ms / 1e3) / 1e12
-        alu_peak = sm_count * 128 * clock_ghz / 1e3  # T simple FP32 ops/s
-        roof = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "Tops/s",
-                "frac": ach / alu_peak, "traffic": None, "kernel": "subtree",
-                "launches": n, "avg_launch_us": ms / n * 1e3,
-                "work_per_launch": f"{F} frames x t*2^t = {F * t * (1 << t)} f/g evaluations",
-                "peak_source": f"{sm_count} SMs x 128 FP32 lanes x {clock_ghz:.2f} GHz",
-                "ns_per_leaf_per_frame": ms * 1e6 / (n * (1 << t)), "timing": prof_mode}
-    else:
-        roof = hbm_roof([dom])
+    roof, roof_streamed = leg_rooflines(prof, F, t, prof_mode, sm_count, clock_ghz,
+                                        sched["node_log2"])
     kernel_share = {k: {"ms": prof[k][0], "launches": prof[k][1]} for k in prof}
 
     cpu = None
@@ -777,14 +771,13 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.prec == "fp32" else "f32 compute, f16 storage",
             "data": "synthetic",
-            "config": config_of(w, args, {"subtree_log2": tuned[0] if tuned else
-                                          (args.subtree_log2 or 14),
-                                          "fused_streamed_steps": bool(tuned[1] & 1) if tuned else
-                                          (args.fuse != 0),
-                                          "subtree_takes_parent_step": bool(tuned[1] & 2)
-                                          if tuned else bool(args.prologue),
-                                          "schedule": "polar_autotune" if tuned else "default"}),
-            "roofline": roof, "roofline_streamed": hbm_roof(["stream_f", "stream_g", "chain"]),
+            "config": config_of(w, args, {"subtree_log2": sched["subtree_log2"],
+                                          "fused_streamed_steps": sched["fused"],
+                                          "subtree_takes_parent_step":
+                                              sched["subtree_takes_parent_step"],
+                                          "node_log2": sched["node_log2"],
+                                          "schedule": sched["source"]}),
+            "roofline": roof, "roofline_streamed": roof_streamed,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": ck, "plain_sc": plain, "plain_sc_noshortcut": plain_diag, "fer": fer,
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
@@ -843,16 +836,21 @@ def serve_sweep(P, dev, requests, pool_n, loads=(0.5, 0.8, 0.95), slots_inflight
 
     rng = np.random.default_rng(0x5EED + 4)
     pool_n = min(pool_n, requests)
-    codes, code_ms, pool = {}, [], []
+    codes, code_ms, host_ms, pool = {}, [], [], []
     for i in range(pool_n):
         log2n, ch, par = served_code_grid(rng)
         key = (log2n, ch, par)
         if key not in codes:
+            # the cache miss: construction on the device in double precision
             t0 = time.perf_counter()
             R = 0.93 * capacity_of(ch, par)
-            codes[key] = P.polar_build_frozen_set(log2n, ch, par, R)
+            codes[key] = P.polar_build_frozen_set_device(log2n, ch, par, R, 0.0)
             P.polar_frozen_set_upload(codes[key], 0)        # resident on the device
             code_ms.append((time.perf_counter() - t0) * 1e3)
+            if len(host_ms) < 8:                            # the host construction beside it
+                t0 = time.perf_counter()
+                P.polar_build_frozen_set(log2n, ch, par, R)
+                host_ms.append(((time.perf_counter() - t0) * 1e3, log2n))
         fs = codes[key]
         N = 1 << log2n
         x, y = S.device_frame(ch, par, N, 0x5EED + 4, i, dev)
@@ -886,22 +884,36 @@ def serve_sweep(P, dev, requests, pool_n, loads=(0.5, 0.8, 0.95), slots_inflight
         assert all(r[0] == P.POLAR_OK for r in res)
         bits = sum(pool[i % pool_n][1] for i in range(len(arrivals)))
         lat = [r[2] for r in res]
-        return wall, bits, lat
+        lens = [pool[i % pool_n][1] for i in range(len(arrivals))]
+        return wall, bits, lat, lens
+
+    def by_length(lat, lens):
+        """Frame latency percentiles per code length (a 2^22 frame takes
+        ~35 ms on one SM however idle the device, a 2^16 frame ~0.5 ms)."""
+        out = {}
+        for N in sorted(set(lens)):
+            v = [a for a, b in zip(lat, lens) if b == N]
+            out[f"2^{N.bit_length() - 1}"] = {"frames": len(v),
+                                               "p50_ms": float(np.percentile(v, 50)),
+                                               "p99_ms": float(np.percentile(v, 99))}
+        return out
 
     def sweep(persistent):
         run([None] * min(64, requests), persistent)                  # warm-up
-        wall, bits, lat = run([None] * requests, persistent)          # saturated
+        wall, bits, lat, lens = run([None] * requests, persistent)    # saturated
         sat_rps = requests / wall
         res = {"saturated": {"mbit_s": bits / wall / 1e6, "req_s": sat_rps,
                              "p50_ms": float(np.percentile(lat, 50)),
-                             "p99_ms": float(np.percentile(lat, 99))}}
+                             "p99_ms": float(np.percentile(lat, 99)),
+                             "by_length": by_length(lat, lens)}}
         for load in loads:
             gaps = rng.exponential(1.0 / (load * sat_rps), requests)
             arrivals = list(np.cumsum(gaps) - gaps[0])
-            wall, bits, lat = run(arrivals, persistent)
+            wall, bits, lat, lens = run(arrivals, persistent)
             res[f"load_{load}"] = {"offered_req_s": load * sat_rps, "mbit_s": bits / wall / 1e6,
                                    "p50_ms": float(np.percentile(lat, 50)),
-                                   "p99_ms": float(np.percentile(lat, 99))}
+                                   "p99_ms": float(np.percentile(lat, 99)),
+                                   "by_length": by_length(lat, lens)}
         return res
 
     launches0 = P.polar_kernel_launches()
@@ -927,8 +939,11 @@ def serve_sweep(P, dev, requests, pool_n, loads=(0.5, 0.8, 0.95), slots_inflight
                              if out_slots else None),
             "fer_sample": errs / min(requests, pool_n),
             "code_build_ms": {"mean": float(np.mean(code_ms)), "max": float(np.max(code_ms)),
-                              "what": "frozen-set cache miss cost (host construction and "
-                                      "upload of the device tables)"}}
+                              "what": "frozen-set cache miss cost: construction on the device "
+                                      "(polar_build_frozen_set_device) and upload of the "
+                                      "node-class tables",
+                              "host_construction_sample": [
+                                  {"log2n": n, "ms": ms} for ms, n in host_ms]}}
 
 
 def run_serve(args):

@@ -184,6 +184,26 @@ int polar_build_frozen_set(uint32_t log2n, polar_channel ch, double param,
 int polar_build_frozen_set_sum(uint32_t log2n, polar_channel ch, double param,
                                double sum_pe_max, polar_frozen_set **out);
 
+/* The construction of polar_build_frozen_set (rate > 0) or of
+ * polar_build_frozen_set_sum (rate = 0, with sum_pe_max), computed on the
+ * current CUDA device in double precision (Sec. 3: frozen bits are the least
+ * reliable bit-channels; the paper suggests moving density evolution to a
+ * parallel device): each polarisation level is one launch, the bit-channels
+ * are ranked by a stable radix sort of (reliability, index) with the lower
+ * index frozen first on equal reliability, and Sec. 3's rule takes a prefix
+ * sum of P_e along the ranking.  Stream-ordered on `stream`, synchronous on
+ * return (the mask is read back to the host; the device copy stays resident
+ * for decodes on this device).  Takes about 2N * 40 bytes of device memory
+ * while it runs.  The device's exp / log / pow round differently from the
+ * host's in the last bit, so the set can differ from the host construction
+ * only at bit-channels whose reliability is within rounding of the K-th one
+ * (and, with the sum rule, K by one where the sum meets the budget within
+ * rounding).  EINVAL as polar_build_frozen_set, or sum_pe_max < 0; ENOMEM;
+ * ECUDA. */
+int polar_build_frozen_set_device(uint32_t log2n, polar_channel ch, double param,
+                                  double rate, double sum_pe_max, void *stream,
+                                  polar_frozen_set **out);
+
 /* Frozen set from the degraded-channel construction (Sec. 3's density
  * evolution made finite, after Tal & Vardy 2013): every bit-channel is
  * tracked as a symmetric channel of at most mu outputs (mu even, 2..128),

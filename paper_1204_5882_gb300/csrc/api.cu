@@ -1070,6 +1070,12 @@ int polar_reveal(const polar_frozen_set *fs_c, int nframes, const uint32_t *x_de
   return POLAR_OK;
 }
 
+int polar_build_frozen_set_device(uint32_t log2n, polar_channel ch, double param, double rate,
+                                  double sum_pe_max, void *stream, polar_frozen_set **out) {
+  return build_frozen_set_device(log2n, ch, param, rate, sum_pe_max,
+                                 static_cast<cudaStream_t>(stream), out);
+}
+
 int polar_sc_decode_many(const polar_frozen_set *fs, int nframes, const float *llr_dev,
                          const uint32_t *frozen_vals_dev, uint32_t *xhat_dev, uint32_t *uhat_dev,
                          polar_fkind fkind, polar_prec prec, void *stream) {

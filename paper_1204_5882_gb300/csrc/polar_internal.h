@@ -89,6 +89,11 @@ int tv_bit_channel_pe(uint32_t log2n, polar_channel ch, double param, int mu,
 int build_frozen_set_tv(uint32_t log2n, polar_channel ch, double param, int mu, double rate,
                         double sum_pe_max, polar_frozen_set **out);
 NodeClass node_class_host(const polar_frozen_set *fs, int k, uint64_t o);
+// Bhattacharyya (BSC) / GA (BI-AWGN) set built on the current device in
+// double precision (construct_dev.cu): K = floor(rate N), or with rate = 0
+// the largest K whose most reliable channels have sum P_e <= sum_max.
+int build_frozen_set_device(uint32_t log2n, polar_channel ch, double param, double rate,
+                            double sum_max, cudaStream_t s, polar_frozen_set **out);
 // fuse: chain kernels for runs of streamed steps; prologue: the subtree
 // kernel performs the streamed step that produces its input; split > t: every
 // node of 2^split leaves that is not rate 0 is one OP_NODE unit (the levels

@@ -77,6 +77,7 @@ def _load():
         "polar_frozen_set_from_mask": ([U32, P, C.POINTER(P)], I),
         "polar_build_frozen_set_tv": ([U32, I, D, I, D, D, C.POINTER(P)], I),
         "polar_build_frozen_set_sum": ([U32, I, D, D, C.POINTER(P)], I),
+        "polar_build_frozen_set_device": ([U32, I, D, D, D, P, C.POINTER(P)], I),
         "polar_frozen_set_query": ([P, C.POINTER(U32), C.POINTER(U64), P, C.POINTER(D)], I),
         "polar_frozen_set_free": ([P], None),
         "polar_llr_from_channel": ([I, D, P, I, P, SZ, P], I),
@@ -214,6 +215,17 @@ def polar_build_frozen_set_sum(log2n: int, channel: str, param: float,
     h = C.c_void_p()
     _check("polar_build_frozen_set_sum", _lib.polar_build_frozen_set_sum(
         int(log2n), CHANNEL[channel], float(param), float(sum_pe_max), C.byref(h)))
+    return FrozenSet(h.value)
+
+
+def polar_build_frozen_set_device(log2n: int, channel: str, param: float, rate: float = 0.0,
+                                  sum_pe_max: float = 0.1, stream=None) -> FrozenSet:
+    """Bhattacharyya / GA set built on the GPU in double precision; K =
+    floor(rate N), or with rate = 0 by the sum rule (Sec. 3)."""
+    h = C.c_void_p()
+    _check("polar_build_frozen_set_device", _lib.polar_build_frozen_set_device(
+        int(log2n), CHANNEL[channel], float(param), float(rate), float(sum_pe_max),
+        _stream(stream), C.byref(h)))
     return FrozenSet(h.value)
 
 
