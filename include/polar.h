@@ -336,9 +336,14 @@ int polar_sc_decode_batch(int nframes, const polar_frame_desc *frames,
  * stream through a per-CTA slice of the workspace, every 2^t-leaf subtree is
  * decoded in shared memory, rate-0 nodes take beta = fv F^{(x)k}.  Frames
  * never wait on one another, so a long frame overlaps many short ones.
- * Results are bit-identical to polar_sc_decode_many (same float32 f and g on
- * the same operands; min-sum x_hat / u_hat equal the float32 oracle).
- * prec: POLAR_FP32 only (POLAR_EINVAL otherwise).  Every llr must be 16-byte
+ * Results are bit-identical to polar_sc_decode_many at the same subtree size
+ * (same f and g on the same operands with the same storage rounding; min-sum
+ * float32 x_hat / u_hat equal the float32 oracle).  prec: POLAR_FP32, or
+ * POLAR_FP16 / POLAR_INT8 storage of the levels above t (rounded, saturated,
+ * int8 with the per-frame scale of the "int8_target" option, formed by the
+ * CTA itself); with reduced storage the results depend on t like those of
+ * polar_sc_decode_many, which rounds the levels above its own subtree size.
+ * Every llr must be 16-byte
  * aligned, frozen_vals / xhat / uhat 4-byte aligned (POLAR_EINVAL).
  * Workspace: the per-stream workspace grows (cudaMalloc) to 256 B + 64 B per
  * frame + CTAs * 4 * (2^nmax - 2^t) bytes (nmax = the longest frame), so the
@@ -404,7 +409,7 @@ double polar_key_rate(double alpha, double fer, double beta, double mutual_info,
  *  - slots (persistent = 0): a scheduler thread launches the oldest pending
  *    request on a free decode slot (a non-blocking CUDA stream with its own
  *    scratch) as soon as a slot is free and the scratch budget allows;
- *  - persistent (persistent = 1, float32 only): one resident launch of the
+ *  - persistent (persistent = 1): one resident launch of the
  *    persistent decoder (see polar_sc_decode_persistent) whose CTAs claim
  *    frames from a ring in host-mapped memory; the scheduler publishes each
  *    admitted request's frames into the ring while the launch runs and reads
@@ -427,7 +432,8 @@ typedef struct {
     polar_prec prec;
     int threads;        /* slots: host scheduler threads launching work, 0 = 4;
                            each owns an equal share of the slots */
-    int persistent;     /* 1 = persistent mode (prec must be POLAR_FP32) */
+    int persistent;     /* 1 = persistent mode (any prec; FP16 / INT8 levels
+                           are rounded above the "persist_log2" subtree size) */
     int max_log2n;      /* persistent: longest code accepted, 1..27, 0 = 22;
                            longer requests are refused at submit (EINVAL) */
 } polar_server_config;

@@ -619,10 +619,7 @@ int check_frames(int nframes, const polar_frame_desc *frames, int fkind, int pre
 int decode_persistent(int nframes, const polar_frame_desc *frames, int fkind, int prec,
                       cudaStream_t s) {
   NvtxRange nv("polar decode persistent");
-  if (prec != POLAR_FP32) {
-    g_last_error = "the persistent decoder keeps float32 levels";
-    return POLAR_EINVAL;
-  }
+  if (prec != POLAR_FP32 && prec != POLAR_FP16 && prec != POLAR_INT8) return POLAR_EINVAL;
   int dev = 0;
   int rc = current_device(&dev);
   if (rc) return rc;
@@ -663,9 +660,9 @@ int decode_persistent(int nframes, const polar_frame_desc *frames, int fkind, in
     nmax = std::max(nmax, n);
     uh |= d.uhat != nullptr;
     const double N = double(uint64_t(1) << n), sl = n - t;
-    alg += (3.0 * sl + 1.0) * N * 4.0 + (0.3125 * sl + 0.375) * N;
+    alg += (3.0 * sl + 1.0) * N * (double)storage_bytes(prec) + (0.3125 * sl + 0.375) * N;
   }
-  const int per_sm = persistent_ctas_per_sm(fkind, uh, tc);
+  const int per_sm = persistent_ctas_per_sm(prec, fkind, uh, tc);
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   if (per_sm < 1 || sms < 1) {
@@ -687,8 +684,8 @@ int decode_persistent(int nframes, const polar_frame_desc *frames, int fkind, in
   CK(cudaMemcpyAsync(ftab, h.data(), (size_t)nframes * sizeof(PFrame), cudaMemcpyHostToDevice,
                      s));
   ProfScope ps(g_cfg.profile.load() != 0, 6, alg, s);
-  CK(launch_persistent(fkind, uh, ftab, (uint32_t)nframes, head, scratch, cta_floats, tc, grid,
-                       s));
+  CK(launch_persistent(prec, fkind, uh, ftab, (uint32_t)nframes, head, scratch, cta_floats, tc,
+                       grid, (double)g_cfg.int8_target.load(), s));
   return POLAR_OK;
 }
 
@@ -1226,7 +1223,10 @@ int polar_tune_load(const char *path) {
                " {\"device\": %d, \"log2n\": %d, \"nframes\": %d, \"fkind\": %d, "
                "\"prec\": %d, \"subtree_log2\": %d, \"fuse\": %d, \"ms\": %lf",
                &k.dev, &k.log2n, &k.nframes, &k.fkind, &k.prec, &v.t, &v.fuse, &v.ms) == 8) {
-      if (v.t < 5 || v.t > 14 || v.fuse < 0 || v.fuse > 3) continue;
+      const int split = (v.fuse >> 8) & 0xFF;   // node-unit level (0: none)
+      if (v.t < 5 || v.t > 14 || v.fuse < 0 || (v.fuse & ~0xFF03) != 0 ||
+          (split != 0 && (split <= v.t || split > 27)))
+        continue;
       g_tune[k] = v;
       ++loaded;
     }

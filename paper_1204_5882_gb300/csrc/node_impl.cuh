@@ -4,9 +4,9 @@
 //
 //   * the steps of the levels s .. t + 1 (f for a left child, g with the left
 //     sibling's partial sums for a right child) run inside the CTA over its
-//     frame's rows of the batch workspace: 16-byte chunks of the stored
-//     values (float, half or int8) are staged into shared memory by cp.async,
-//     several stages in flight per thread, and written back with st.global.cg;
+//     frame's rows of the batch workspace (cta_step: 16-byte chunks of the
+//     stored float, half or int8 values staged into shared memory by
+//     cp.async, written back with st.global.cg);
 //   * every subtree of 2^t leaves is decoded by subtree_body, from the
 //     workspace's level t;
 //   * rate-0 nodes above t take beta = fv F^{(x)k} directly, and steps whose
@@ -22,6 +22,7 @@
 // dependency overhead of many short launches.
 #pragma once
 
+#include "cta_step.cuh"
 #include "subtree_impl.cuh"
 
 namespace polar {
@@ -58,77 +59,6 @@ __device__ __forceinline__ int node_class(const NodeParams &p, int k, uint64_t o
   const uint32_t uw = upper_class_words(p.n, p.t);
   if ((p.ucls[uw + (i >> 5)] >> (i & 31)) & 1u) return NODE_RATE1;
   return NODE_MIXED;
-}
-
-// One step level k -> k-1 over h = 2^(k-1) stored values of this frame:
-//   f (G = false): c[j] = f(a[j], a[j + h]);
-//   g (G = true):  c[j] = g(a[j], a[j + h], bit j of beta).
-// A 48-byte slot per thread and stage holds the 16-byte chunk of a, the one
-// of a + h and (g) the partial-sum word; STG stages stay in flight.
-template <int STG, typename S, int FK, bool G>
-__device__ void node_step(const S *__restrict__ a, S *__restrict__ c, uint32_t h,
-                          const uint32_t *__restrict__ beta, float sc, float4 *stage) {
-  constexpr uint32_t PER = 16 / sizeof(S);        // values per 16-byte chunk
-  const uint4 *x4 = reinterpret_cast<const uint4 *>(a);
-  const uint4 *y4 = reinterpret_cast<const uint4 *>(a + h);
-  uint4 *c4 = reinterpret_cast<uint4 *>(c);
-  const uint32_t hc = h / PER, tid = threadIdx.x;
-  float4 *mine = stage + 3 * tid;
-  const uint32_t iters = (hc + NT - 1) / NT;
-#pragma unroll
-  for (uint32_t it = 0; it < (uint32_t)STG; ++it) {
-    const uint32_t i = it * NT + tid;
-    float4 *sl = mine + it * 3 * NT;
-    if (i < hc) {
-      cp16(sl, x4 + i);
-      cp16(sl + 1, y4 + i);
-      if (G) cp4(sl + 2, beta + ((PER * i) >> 5));
-    }
-    cp_commit();
-  }
-  for (uint32_t it = 0; it < iters; ++it) {
-    cp_wait<STG - 1>();                           // this thread's group `it` has landed
-    const uint32_t i = it * NT + tid;
-    float4 *sl = mine + (it % STG) * 3 * NT;
-    if (i < hc) {
-      const uint4 xv = *reinterpret_cast<const uint4 *>(sl);
-      const uint4 yv = *reinterpret_cast<const uint4 *>(sl + 1);
-      const S *xs = reinterpret_cast<const S *>(&xv);
-      const S *ys = reinterpret_cast<const S *>(&yv);
-      uint4 ov;
-      S *os = reinterpret_cast<S *>(&ov);
-      const uint32_t w = G ? *reinterpret_cast<const uint32_t *>(sl + 2) : 0u;
-      const int j0 = (int)((PER * i) & 31u);
-#pragma unroll
-      for (uint32_t q = 0; q < PER; ++q) {
-        const float xa = Store<S>::ld(xs + q), yb = Store<S>::ld(ys + q);
-        const float v = G ? g_bit(xa, yb, w, j0 + (int)q) : f_st<S, FK>(xa, yb, sc);
-        Store<S>::st(os + q, v);
-      }
-      __stcg(c4 + i, ov);
-    }
-    const uint32_t in = (it + STG) * NT + tid;    // refill the slot just read
-    if (in < hc) {
-      cp16(sl, x4 + in);
-      cp16(sl + 1, y4 + in);
-      if (G) cp4(sl + 2, beta + ((PER * in) >> 5));
-    }
-    cp_commit();
-  }
-  cp_wait<0>();
-  __syncthreads();
-}
-
-template <typename S, int FK, bool G>
-__device__ void node_step_n(int stg, const S *a, S *c, uint32_t h, const uint32_t *beta,
-                            float sc, float4 *stage) {
-  switch (stg) {
-    case 16: node_step<16, S, FK, G>(a, c, h, beta, sc, stage); break;
-    case 8: node_step<8, S, FK, G>(a, c, h, beta, sc, stage); break;
-    case 4: node_step<4, S, FK, G>(a, c, h, beta, sc, stage); break;
-    case 2: node_step<2, S, FK, G>(a, c, h, beta, sc, stage); break;
-    default: node_step<1, S, FK, G>(a, c, h, beta, sc, stage); break;
-  }
 }
 
 // Rate-0 node of 2^k leaves (k >= 5) at leaf o of one frame's rows.
@@ -188,8 +118,9 @@ __global__ void __launch_bounds__(NT, 1) k_node(NodeParams p) {
         break;
       }
       if (node_class(p, k - 1, o) != NODE_RATE0)
-        node_step_n<S, FK, false>(p.stages, node_level<S>(p, k, fr), node_level<S>(p, k - 1, fr),
-                                  1u << (k - 1), nullptr, sc, stage);
+        cta_step_n<NT, S, S, FK, false>(p.stages, node_level<S>(p, k, fr),
+                                        node_level<S>(p, k - 1, fr), 1u << (k - 1), nullptr, sc,
+                                        stage);
       --k;
     }
     int r = 0;                                    // ascend through right children
@@ -201,8 +132,9 @@ __global__ void __launch_bounds__(NT, 1) k_node(NodeParams p) {
     }
     if (k == p.s) break;
     if (node_class(p, k, o + (uint64_t(1) << k)) != NODE_RATE0)
-      node_step_n<S, FK, true>(p.stages, node_level<S>(p, k + 1, fr), node_level<S>(p, k, fr),
-                               1u << k, xrow + (o >> 5), sc, stage);
+      cta_step_n<NT, S, S, FK, true>(p.stages, node_level<S>(p, k + 1, fr),
+                                     node_level<S>(p, k, fr), 1u << k, xrow + (o >> 5), sc,
+                                     stage);
     o += uint64_t(1) << k;
   }
   if (p.r > 0) cascade_device(xrow, p.s, p.o, p.r);
@@ -213,13 +145,6 @@ __global__ void __launch_bounds__(NT, 1) k_node(NodeParams p) {
 inline size_t node_smem_bytes(int t) {
   const size_t sub = bit_words(t) * sizeof(uint32_t) + 2 * (size_t(1) << t) * sizeof(float);
   return sub > size_t(48) * NT ? sub : size_t(48) * NT;
-}
-
-inline int node_stages(size_t smem_bytes) {
-  const size_t per = 48 * NT;
-  int s = 1;
-  while (s < 16 && (size_t)(2 * s) * per <= smem_bytes) s *= 2;
-  return s;
 }
 
 template <typename S, int FK, bool UH>
@@ -233,7 +158,7 @@ cudaError_t launch_node_t(const NodeArgs &a, cudaStream_t s) {
   }
   NodeParams p{a.lv,   a.nframes, a.mask,     a.cls, a.ucls, a.scale, a.fv,
                a.xhat, a.uhat,    a.w_stride, a.o,   a.s,    a.t,     a.n,
-               a.r,    node_stages(smem)};
+               a.r,    step_stages<S, S>(smem, NT)};
   return counted(launch_k(kern, a.nframes, NT, smem, s, p), 1);
 }
 

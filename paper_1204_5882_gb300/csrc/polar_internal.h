@@ -224,13 +224,15 @@ constexpr int kPersistThreads = 128;
 // Dynamic shared memory of a persistent CTA for subtrees of up to 2^t leaves.
 size_t persistent_smem_bytes(int t);
 // Resident CTAs per SM of the persistent kernel (0 on error).
-int persistent_ctas_per_sm(int fkind, bool uhat, int t);
+int persistent_ctas_per_sm(int prec, int fkind, bool uhat, int t);
 // Frames [0, count) of `frames` (device) are claimed in order through *head
-// (device, zero on entry) by `grid` CTAs; CTA c keeps its levels at
-// scratch + c * cta_floats.
-cudaError_t launch_persistent(int fkind, bool uhat, const PFrame *frames, uint32_t count,
-                              uint32_t *head, float *scratch, uint64_t cta_floats, int t,
-                              int grid, cudaStream_t s);
+// (device, zero on entry) by `grid` CTAs; CTA c keeps its levels (stored as
+// prec: float, half or int8) at scratch + c * cta_floats floats; int8 frames
+// take the per-frame scale of the "int8_target" option.
+cudaError_t launch_persistent(int prec, int fkind, bool uhat, const PFrame *frames,
+                              uint32_t count, uint32_t *head, float *scratch,
+                              uint64_t cta_floats, int t, int grid, double int8_target,
+                              cudaStream_t s);
 
 // Serving launch: frames come from a ring in host-mapped memory that the
 // host fills while the launch runs (see persist.cu).
@@ -244,15 +246,16 @@ struct ServeArgs {
   float *scratch;          // grid * cta_floats floats
   uint64_t cta_floats;
   uint64_t idle_ns;        // a CTA leaves after this long without a frame
-  int S;                   // set by launch_serve
+  double int8_target;      // int8 storage: target of the per-frame scale
+  uint32_t smem;           // set by launch_serve
 };
-int serve_ctas_per_sm(int fkind, int t);
+int serve_ctas_per_sm(int prec, int fkind, int t);
 // Make a frozen set resident on `dev` for decodes at subtree size t: its
 // mask, the node-class table of the subtrees (t >= 5) and, with `upper`, the
 // class table of the levels above t that the persistent decoder reads.
 // Switches to `dev` for the uploads and back.  OK, ENOMEM or ECUDA.
 int prepare_tables(polar_frozen_set *fs, int dev, int t, bool upper);
-cudaError_t launch_serve(int fkind, ServeArgs a, int t, int grid, cudaStream_t s);
+cudaError_t launch_serve(int prec, int fkind, ServeArgs a, int t, int grid, cudaStream_t s);
 
 // api.cu: decoding with caller-provided device mask and level scratch.
 size_t level_scratch_bytes(const polar_frozen_set *fs, int nframes, int prec, int *t_out);

@@ -334,8 +334,12 @@ int ring_launch(polar_server *s) {
   a.scratch = r.scratch;
   a.cta_floats = r.cta_floats;
   a.idle_ns = 50000000;
-  a.S = 0;
-  cudaError_t e = polar::launch_serve((int)s->cfg.fkind, a, r.t, r.grid, r.stream);
+  long target = 8;
+  polar_config_get("int8_target", &target);
+  a.int8_target = (double)target;
+  a.smem = 0;
+  cudaError_t e =
+      polar::launch_serve((int)s->cfg.prec, (int)s->cfg.fkind, a, r.t, r.grid, r.stream);
   if (e == cudaSuccess) e = cudaEventRecord(r.ev, r.stream);
   if (e != cudaSuccess) {
     polar::set_last_error(cudaGetErrorString(e));
@@ -406,7 +410,7 @@ int ring_create(polar_server *s) {
   polar_config_get("persist_log2", &tcfg);
   r.t = (int)tcfg;
   const int nmax = c.max_log2n ? c.max_log2n : 22;
-  const int per_sm = polar::serve_ctas_per_sm((int)c.fkind, r.t);
+  const int per_sm = polar::serve_ctas_per_sm((int)c.prec, (int)c.fkind, r.t);
   int sms = 0;
   if (per_sm < 1 || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device) !=
                         cudaSuccess) {
@@ -464,8 +468,7 @@ int polar_server_create(const polar_server_config *cfg, polar_server **out) {
   if (cfg->max_inflight < 1 || cfg->max_inflight > (cfg->persistent ? 4096 : 256) ||
       cfg->max_queue < 1)
     return POLAR_EINVAL;
-  if (cfg->persistent && (cfg->prec != POLAR_FP32 || cfg->max_log2n < 0 || cfg->max_log2n > 27))
-    return POLAR_EINVAL;
+  if (cfg->persistent && (cfg->max_log2n < 0 || cfg->max_log2n > 27)) return POLAR_EINVAL;
   if (cfg->fkind != POLAR_F_MINSUM && cfg->fkind != POLAR_F_EXACT) return POLAR_EINVAL;
   if (cfg->prec != POLAR_FP32 && cfg->prec != POLAR_FP16 && cfg->prec != POLAR_INT8)
     return POLAR_EINVAL;

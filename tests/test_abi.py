@@ -91,12 +91,12 @@ def test_argument_errors_are_host_side(P):
     assert L.polar_frame_hash(10, 1, None, 1, 16, None) == P.POLAR_EINVAL
     assert L.polar_frame_hash(10, 1, 16, 1, 12, None) == P.POLAR_EINVAL
     assert P.polar_key_rate(0.5, 0.1, 0.9, 0.8, 0.3) == pytest.approx(0.5 * 0.9 * (0.9 * 0.8 - 0.3))
-    # persistent decoder: empty queue, null table, non-float32 storage
+    # persistent decoder: empty queue, null table, unknown storage
     desc = (P.FrameDesc * 1)(P.FrameDesc(fs.handle.value, 16, 16, 16, None))
     assert L.polar_sc_decode_persistent(0, desc, 0, 0, None) == P.POLAR_EINVAL
     assert L.polar_sc_decode_persistent(1, None, 0, 0, None) == P.POLAR_EINVAL
-    assert L.polar_sc_decode_persistent(1, desc, 0, 1, None) == P.POLAR_EINVAL
-    assert L.polar_sc_decode_persistent(1, desc, 0, 2, None) == P.POLAR_EINVAL
+    assert L.polar_sc_decode_persistent(1, desc, 0, 3, None) == P.POLAR_EINVAL
+    assert L.polar_sc_decode_persistent(1, desc, 0, -1, None) == P.POLAR_EINVAL
     bad = (P.FrameDesc * 1)(P.FrameDesc(fs.handle.value, 20, 16, 16, None))   # llr not 16-B
     assert L.polar_sc_decode_persistent(1, bad, 0, 0, None) == P.POLAR_EINVAL
     with pytest.raises(P.PolarError):

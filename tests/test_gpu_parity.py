@@ -386,7 +386,10 @@ def test_autotune_picks_a_schedule_and_keeps_results(P):
     xh = torch.zeros_like(xd)
     P.polar_tune_clear()
     t, fuse, ms = P.polar_autotune(fs, w.frames, llr, fv, xh)
-    assert t in (12, 13, 14) and fuse in (0, 1, 2, 3) and ms > 0
+    split = (fuse >> 8) & 0xFF          # node-unit level, 0 = none
+    assert t in (12, 13, 14) and (fuse & 0xFF) in (0, 1, 2, 3) and ms > 0
+    assert split == 0 or t < split <= min(w.log2n - 1, t + 4)
+    assert fuse >> 16 == 0
     xh2 = torch.zeros_like(xd)
     P.polar_sc_decode_many(fs, w.frames, llr, fv, xh2)       # uses the tuned schedule
     torch.cuda.synchronize()

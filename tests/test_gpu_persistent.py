@@ -31,7 +31,8 @@ def P():
 
 @pytest.fixture(autouse=True)
 def default_config(P):
-    saved = {k: P.polar_config_get(k) for k in ("persist_log2", "persistent", "subtree_log2")}
+    saved = {k: P.polar_config_get(k)
+             for k in ("persist_log2", "persistent", "subtree_log2", "autotune")}
     yield
     for k, v in saved.items():
         P.polar_config_set(k, v)
@@ -226,3 +227,38 @@ def test_upload_makes_a_code_resident_before_its_first_decode(P):
     P.polar_sc_decode_persistent(frames)
     torch.cuda.synchronize()
     check_against_oracle(frames, inputs)
+
+
+@pytest.mark.parametrize("prec", ["fp16", "int8"])
+@pytest.mark.parametrize("fkind", ["minsum", "exact"])
+@pytest.mark.parametrize("t", [9, 13])
+def test_reduced_storage_persistent(P, prec, fkind, t):
+    """FP16 / INT8 levels in the persistent decoder: bit-identical to the
+    launched schedule at the same subtree size (the levels >= t stored and
+    rounded alike, int8 with the same per-frame scale), and min-sum equal to
+    the oracle's storage model."""
+    rng = np.random.default_rng(500 + t)
+    specs = [(n, kind, "gauss") for n in (5, 9, 12, 14, 16) for kind in ("polar", "random")]
+    specs += [(15, "front_frozen", "bsc"), (13, "low_rate", "gauss")]
+    frames, inputs = make_frames(P, rng, specs)
+    P.polar_config_set("persist_log2", t)
+    P.polar_sc_decode_persistent(frames, fkind=fkind, prec=prec)
+    torch.cuda.synchronize()
+    P.polar_config_set("autotune", 0)
+    P.polar_config_set("subtree_log2", t)
+    try:
+        target = P.polar_config_get("int8_target")
+        for (fs, llr, fv, xh, uh), (L, fz, fvb) in zip(frames, inputs):
+            rx, ru = torch.full_like(fv, -1), torch.full_like(fv, -1)
+            P.polar_sc_decode_many(fs, 1, llr, fv, rx, ru, fkind, prec)
+            torch.cuda.synchronize()
+            assert torch.equal(xh, rx), (fs.log2n, prec, fkind)
+            if uh is not None:
+                assert torch.equal(uh, ru), (fs.log2n, prec, fkind)
+            if fkind == "minsum":
+                sc = O.int8_scale(L, target) if prec == "int8" else 1.0
+                ou, ox = O.sc_decode_store(L, fz, fvb, "minsum", prec, sc,
+                                           min_level=min(fs.log2n, t))
+                assert np.array_equal(S.unpack_bits(words_np(xh), fs.N), ox), fs.log2n
+    finally:
+        P.polar_config_set("autotune", 1)

@@ -55,18 +55,31 @@ def make_requests(P, count, seed, sizes=(10, 12, 14, 16)):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("persistent", [False, True])
-def test_results_identical_alone_and_in_mix(P, persistent):
+@pytest.mark.parametrize("persistent,prec", [(False, "fp32"), (True, "fp32"), (True, "fp16"),
+                                             (True, "int8")])
+def test_results_identical_alone_and_in_mix(P, persistent, prec):
+    """A request decoded in the mix equals the same request decoded alone.
+    Reduced storage rounds the levels above the subtree size, so the lone
+    decodes use the persistent server's subtree size ("persist_log2")."""
     reqs = make_requests(P, 40, 11)
     stream = torch.cuda.Stream()
     alone = []
-    for r in reqs:                                   # one at a time, synchronously
-        xh = torch.zeros_like(r["fv"])
-        P.polar_sc_decode_many(r["fs"], r["F"], r["llr"], r["fv"], xh, None, "minsum", "fp32",
-                               stream)
-        stream.synchronize()
-        alone.append(xh.cpu())
-    srv = P.Server(max_inflight=16, max_queue=1024, persistent=persistent, max_log2n=16)
+    saved = {k: P.polar_config_get(k) for k in ("autotune", "subtree_log2")}
+    if prec != "fp32":
+        P.polar_config_set("autotune", 0)
+        P.polar_config_set("subtree_log2", P.polar_config_get("persist_log2"))
+    try:
+        for r in reqs:                               # one at a time, synchronously
+            xh = torch.zeros_like(r["fv"])
+            P.polar_sc_decode_many(r["fs"], r["F"], r["llr"], r["fv"], xh, None, "minsum", prec,
+                                   stream)
+            stream.synchronize()
+            alone.append(xh.cpu())
+    finally:
+        for k, v in saved.items():
+            P.polar_config_set(k, v)
+    srv = P.Server(max_inflight=16, max_queue=1024, persistent=persistent, max_log2n=16,
+                   prec=prec)
     outs, tickets = [], []
     for r in reqs:
         outs.append(torch.full_like(r["fv"], -1))
@@ -83,6 +96,8 @@ def test_results_identical_alone_and_in_mix(P, persistent):
     assert stats["completed"] == len(reqs)
     for r, a, b in zip(reqs, alone, outs):
         assert torch.equal(a, b.cpu())
+    if prec != "fp32":
+        return
     for r, b in list(zip(reqs, outs))[:6]:           # and the oracle agrees
         got = b.cpu().numpy().view(np.uint32)
         for f in range(r["F"]):
