@@ -748,6 +748,12 @@ def run_ours(args):
     clock_ghz = (ck.get("sm_max_mhz") or 2070.0) / 1e3
     roof, roof_streamed = leg_rooflines(prof, F, t, prof_mode, sm_count, clock_ghz,
                                         sched["node_log2"])
+    if (roof and w.name == "bsc_p03_n20" and F == 64 and t == 14 and sched["node_log2"] == 0
+            and args.fkind == "minsum" and args.prec == "fp32"):
+        # DRAM bytes per k_subtree launch of this schedule from one ncu capture
+        # (dram__bytes_read.sum + dram__bytes_write.sum; profiles/k_subtree_bsc_p03_n20.md)
+        roof["traffic"] = 4467968.0
+        roof["traffic_source"] = "ncu capture of this kernel and schedule (one launch)"
     kernel_share = {k: {"ms": prof[k][0], "launches": prof[k][1]} for k in prof}
 
     cpu = None

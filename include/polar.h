@@ -187,8 +187,9 @@ int polar_build_frozen_set_sum(uint32_t log2n, polar_channel ch, double param,
 /* The construction of polar_build_frozen_set (rate > 0) or of
  * polar_build_frozen_set_sum (rate = 0, with sum_pe_max), computed on the
  * current CUDA device in double precision (Sec. 3: frozen bits are the least
- * reliable bit-channels; the paper suggests moving density evolution to a
- * parallel device): each polarisation level is one launch, the bit-channels
+ * reliable bit-channels; on the device a new code costs milliseconds, which
+ * makes it the request server's cache miss): each polarisation level is one
+ * launch, the bit-channels
  * are ranked by a stable radix sort of (reliability, index) with the lower
  * index frozen first on equal reliability, and Sec. 3's rule takes a prefix
  * sum of P_e along the ranking.  Stream-ordered on `stream`, synchronous on

@@ -214,206 +214,238 @@ int build_frozen_set_sum(uint32_t log2n, polar_channel ch, double param, double 
 }
 
 // ---------------------------------------------------------------- degraded construction
-// Sec. 3's density evolution made finite (Tal & Vardy, "How to construct
-// polar codes", 2013): every bit-channel is held as at most M = mu/2
-// conjugate output pairs (a, b), a >= b (a = W(y|0) = W(y'|1)), degraded
-// with respect to the true bit-channel, so its ML error probability sum b is
-// an upper bound that tightens with mu.  From pairs i <= j of a channel
-// (doubled when i < j, for the orders (i, j) and (j, i)):
-//   minus: (a_i a_j + b_i b_j, a_i b_j + b_i a_j)
-//   plus:  (a_i a_j, b_i b_j) and (max, min)(a_i b_j, b_i a_j).
-// The products are sorted by likelihood ratio and the neighbours whose
-// merger loses the least mutual information are merged (the first such
-// neighbour on ties) until M pairs remain.  The BI-AWGN channel starts as
-// 4M pairs cut from y >= 0 at equal steps of capacity contribution.  The
-// tree is walked depth first from 64 subtree roots, in parallel; every leaf
-// is computed by the same sequence of operations whatever the thread.
+// Sec. 3's density evolution made finite after Tal & Vardy ("How to construct
+// polar codes", 2013).  A binary-input symmetric channel is a mixture of
+// BSCs: each conjugate output pair is one class with probability mass w and
+// crossover z <= 1/2 (the error probability of the ML decision on that pair),
+// and the channel's error probability is sum w z.  For two independent looks
+// at classes (w1, z1), (w2, z2):
+//   check node (minus):  one class, mass w1 w2, crossover z1 (1-z2) + z2 (1-z1);
+//   variable node (plus): the looks agree -- mass w1 w2 ((1-z1)(1-z2) + z1 z2),
+//                         crossover z1 z2 / that sum -- or disagree -- mass
+//                         w1 w2 (z1 (1-z2) + z2 (1-z1)), crossover the smaller
+//                         of the two products / that sum.
+// Merging two classes into (w1 + w2, (w1 z1 + w2 z2) / (w1 + w2)) gives a
+// channel degraded with respect to the original, so every error probability
+// computed here bounds the true one from above.  A channel is kept at M = mu/2
+// classes: they are ordered by crossover and the neighbours whose merger
+// loses the least capacity, w1 C(z1) + w2 C(z2) - (w1 + w2) C(z12) with
+// C(z) = 1 - h2(z), are merged first (on equal loss the pair of larger
+// crossover), which is Tal and Vardy's greedy merging.  A BI-AWGN start is cut into 4M classes
+// by |LLR| thresholds at which the BSC capacity 1 - h2(1 / (1 + e^|l|)) steps
+// by 1 / (4M).  Every leaf of the tree is computed by the same operations in
+// the same order whichever thread walks it.
 namespace {
 
-struct TvPair {
-  double a, b;
+struct Cls {
+  double w, z;
 };
 
-double tv_info(const TvPair &p) {
-  const double s = p.a + p.b;
-  double r = 0.0;
-  if (p.a > 0.0) r += p.a * std::log2(2.0 * p.a / s);
-  if (p.b > 0.0) r += p.b * std::log2(2.0 * p.b / s);
-  return r;
+inline double h2(double z) {
+  double h = 0.0;
+  if (z > 0.0) h -= z * std::log2(z);
+  if (z < 1.0) h -= (1.0 - z) * std::log2(1.0 - z);
+  return h;
+}
+inline double cap_of(const Cls &c) { return c.w * (1.0 - h2(c.z)); }
+
+inline Cls merged(const Cls &x, const Cls &y) {
+  const double w = x.w + y.w;
+  return Cls{w, w > 0.0 ? (x.w * x.z + y.w * y.z) / w : 0.0};
 }
 
-// Likelihood ratio a/b ascending (b = 0 last), then a, then b.
-bool tv_before(const TvPair &x, const TvPair &y) {
-  const double l = x.a * y.b, r = y.a * x.b;
-  if (l != r) return l < r;
-  if (x.a != y.a) return x.a < y.a;
-  return x.b < y.b;
-}
-
-struct TvScratch {
-  std::vector<TvPair> prod;
-  std::vector<double> info, loss;
-  explicit TvScratch(int cap) : prod(cap), info(cap), loss(cap) {}
-};
-
-int tv_reduce(TvPair *p, int L, int M, TvScratch &w) {
-  int c = 0;
-  for (int k = 0; k < L; ++k)
-    if (p[k].a + p[k].b > 0.0) p[c++] = p[k];
-  L = c;
-  std::sort(p, p + L, tv_before);
-  if (L <= M) return L;
-  double *info = w.info.data(), *loss = w.loss.data();
-  for (int k = 0; k < L; ++k) info[k] = tv_info(p[k]);
-  auto merged_loss = [&](int k) {
-    const TvPair m{p[k].a + p[k + 1].a, p[k].b + p[k + 1].b};
-    return info[k] + info[k + 1] - tv_info(m);
-  };
-  for (int k = 0; k + 1 < L; ++k) loss[k] = merged_loss(k);
-  while (L > M) {
-    int best = 0;
-    for (int k = 1; k + 1 < L; ++k)
-      if (loss[k] < loss[best]) best = k;
-    p[best].a += p[best + 1].a;
-    p[best].b += p[best + 1].b;
-    info[best] = tv_info(p[best]);
-    for (int k = best + 1; k + 1 < L; ++k) {
-      p[k] = p[k + 1];
-      info[k] = info[k + 1];
-    }
-    for (int k = best + 1; k + 2 < L; ++k) loss[k] = loss[k + 1];
-    --L;
-    for (int k = std::max(best - 1, 0); k <= best && k + 1 < L; ++k) loss[k] = merged_loss(k);
-  }
-  return L;
-}
-
-int tv_child(const TvPair *w, int L, bool plus, TvPair *out) {
-  int c = 0;
-  for (int i = 0; i < L; ++i)
-    for (int j = i; j < L; ++j) {
-      const double f = (i == j) ? 1.0 : 2.0;
+// Classes of the check-node / variable-node channel of two looks at c[0..L).
+// Unordered pairs i <= j; i != j counts both orders.
+size_t combine(const Cls *c, size_t L, bool plus, Cls *out) {
+  size_t m = 0;
+  for (size_t i = 0; i < L; ++i) {
+    for (size_t j = i; j < L; ++j) {
+      const double mass = (i == j ? 1.0 : 2.0) * c[i].w * c[j].w;
+      const double zi = c[i].z, zj = c[j].z;
       if (!plus) {
-        out[c].a = f * (w[i].a * w[j].a + w[i].b * w[j].b);
-        out[c].b = f * (w[i].a * w[j].b + w[i].b * w[j].a);
-        ++c;
-      } else {
-        const double x = w[i].a * w[j].b, y = w[i].b * w[j].a;
-        out[c].a = f * w[i].a * w[j].a;
-        out[c].b = f * w[i].b * w[j].b;
-        ++c;
-        out[c].a = f * (x > y ? x : y);
-        out[c].b = f * (x > y ? y : x);
-        ++c;
+        out[m++] = Cls{mass, zi * (1.0 - zj) + zj * (1.0 - zi)};
+        continue;
+      }
+      const double agree = (1.0 - zi) * (1.0 - zj) + zi * zj;
+      const double p1 = zi * (1.0 - zj), p2 = zj * (1.0 - zi), differ = p1 + p2;
+      if (agree > 0.0) out[m++] = Cls{mass * agree, zi * zj / agree};
+      if (differ > 0.0) out[m++] = Cls{mass * differ, std::min(p1, p2) / differ};
+    }
+  }
+  return m;
+}
+
+// Greedy merging down to at most M classes.  A min-heap holds each adjacent
+// pair's loss keyed by (loss, position of its left class); merged-away or
+// stale entries are skipped when they surface.
+struct Merger {
+  std::vector<Cls> cls;
+  std::vector<int> prev, next;
+  std::vector<uint32_t> stamp;
+  struct Item {
+    double loss;
+    int left;
+    uint32_t s1, s2;
+    bool operator>(const Item &o) const {
+      return loss != o.loss ? loss > o.loss : left > o.left;
+    }
+  };
+  std::vector<Item> heap;
+
+  size_t run(Cls *c, size_t L, size_t M) {
+    size_t n = 0;
+    for (size_t k = 0; k < L; ++k)
+      if (c[k].w > 0.0) c[n++] = c[k];
+    // likelihood ratio (1 - z) / z ascending: crossover descending, then mass
+    std::sort(c, c + n, [](const Cls &x, const Cls &y) {
+      return x.z != y.z ? x.z > y.z : x.w < y.w;
+    });
+    if (n <= M) return n;
+    cls.assign(c, c + n);
+    prev.resize(n);
+    next.resize(n);
+    stamp.assign(n, 0u);
+    for (size_t k = 0; k < n; ++k) {
+      prev[k] = (int)k - 1;
+      next[k] = k + 1 < n ? (int)k + 1 : -1;
+    }
+    auto loss_at = [&](int l) {
+      const int r = next[l];
+      return cap_of(cls[l]) + cap_of(cls[r]) - cap_of(merged(cls[l], cls[r]));
+    };
+    heap.clear();
+    for (int k = 0; k + 1 < (int)n; ++k) heap.push_back(Item{loss_at(k), k, 0u, 0u});
+    std::make_heap(heap.begin(), heap.end(), std::greater<Item>());
+    size_t live = n;
+    while (live > M && !heap.empty()) {
+      std::pop_heap(heap.begin(), heap.end(), std::greater<Item>());
+      const Item it = heap.back();
+      heap.pop_back();
+      const int l = it.left, r = next[l];
+      if (r < 0 || stamp[l] != it.s1 || stamp[r] != it.s2) continue;   // stale
+      cls[l] = merged(cls[l], cls[r]);
+      ++stamp[l];
+      stamp[r] = 0xFFFFFFFFu;                       // gone
+      next[l] = next[r];
+      if (next[r] >= 0) prev[next[r]] = l;
+      --live;
+      if (prev[l] >= 0) {
+        const int q = prev[l];
+        heap.push_back(Item{loss_at(q), q, stamp[q], stamp[l]});
+        std::push_heap(heap.begin(), heap.end(), std::greater<Item>());
+      }
+      if (next[l] >= 0) {
+        heap.push_back(Item{loss_at(l), l, stamp[l], stamp[next[l]]});
+        std::push_heap(heap.begin(), heap.end(), std::greater<Item>());
       }
     }
-  return c;
-}
-
-double tv_cap_llr(double l) {   // 1 - h2(1 / (1 + e^l))
-  const double q = 1.0 / (1.0 + std::exp(l));
-  if (q <= 0.0) return 1.0;
-  return 1.0 + q * std::log2(q) + (1.0 - q) * std::log2(1.0 - q);
-}
-
-double tv_q(double x) { return 0.5 * std::erfc(x / M_SQRT2); }
-
-int tv_start(polar_channel ch, double param, int M0, TvPair *p) {
-  if (ch == POLAR_BSC) {
-    p[0] = TvPair{1.0 - param, param};
-    return 1;
+    size_t m = 0;
+    for (int k = 0; k >= 0; k = next[k]) c[m++] = cls[k];
+    return m;
   }
-  const double s2 = param, sg = std::sqrt(param);
-  double lo_y = 0.0;
-  for (int k = 0; k < M0; ++k) {
-    double hi_y = INFINITY;
-    if (k + 1 < M0) {
-      const double target = (double)(k + 1) / M0;
-      double lo = 0.0, hi = 1.0;
-      while (tv_cap_llr(hi) < target) hi *= 2.0;
-      for (int it = 0; it < 200; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (mid <= lo || mid >= hi) break;
-        if (tv_cap_llr(mid) < target) lo = mid;
-        else hi = mid;
-      }
-      hi_y = hi * s2 / 2.0;
-    }
-    const double qa_hi = std::isinf(hi_y) ? 0.0 : tv_q((hi_y - 1.0) / sg);
-    const double qb_hi = std::isinf(hi_y) ? 0.0 : tv_q((hi_y + 1.0) / sg);
-    p[k].a = tv_q((lo_y - 1.0) / sg) - qa_hi;
-    p[k].b = tv_q((lo_y + 1.0) / sg) - qb_hi;
-    lo_y = hi_y;
-  }
-  return M0;
-}
-
-struct TvTree {
-  int n, M;
-  double *pe;
 };
 
-// Depth-first below node (depth s, index j) whose channel is `w` (L pairs).
-void tv_walk(const TvTree &T, const TvPair *w, int L, int s, uint64_t j,
-             std::vector<TvPair> &stack, TvScratch &sc) {
-  if (s == T.n) {
-    double e = 0.0;
-    for (int k = 0; k < L; ++k) e += w[k].b;
-    T.pe[j] = e;
-    return;
+inline double gauss_tail(double x) { return 0.5 * std::erfc(x / M_SQRT2); }
+
+// |LLR| at which the BSC of crossover 1 / (1 + e^l) has capacity c (0 < c < 1).
+double llr_at_capacity(double c) {
+  // 1 - h2(z) = c for z in (0, 1/2): h2 is increasing there, bisect on z
+  double lo = 0.0, hi = 0.5;
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (1.0 - h2(mid) > c) lo = mid;
+    else hi = mid;
   }
-  TvPair *child = stack.data() + (size_t)(s + 1) * T.M;
-  for (int side = 0; side < 2; ++side) {
-    int c = tv_child(w, L, side == 1, sc.prod.data());
-    c = tv_reduce(sc.prod.data(), c, T.M, sc);
-    std::copy(sc.prod.begin(), sc.prod.begin() + c, child);
-    tv_walk(T, child, c, s + 1, 2 * j + side, stack, sc);
-  }
+  const double z = 0.5 * (lo + hi);
+  return std::log((1.0 - z) / z);
 }
+
+// The channel's starting classes.
+std::vector<Cls> start_classes(polar_channel ch, double param, size_t M0) {
+  if (ch == POLAR_BSC) return {Cls{1.0, param}};
+  const double sg = std::sqrt(param);
+  std::vector<Cls> out;
+  double y0 = 0.0;                                  // class k: |y| in [y0, y1)
+  for (size_t k = 0; k < M0; ++k) {
+    const double y1 =
+        k + 1 < M0 ? llr_at_capacity((double)(k + 1) / (double)M0) * param / 2.0 : INFINITY;
+    // mass given x = 0 (y ~ N(1, s2)) on y in [y0, y1) (a) and y in (-y1, -y0] (b)
+    const double a = gauss_tail((y0 - 1.0) / sg) - (std::isinf(y1) ? 0.0 : gauss_tail((y1 - 1.0) / sg));
+    const double b = gauss_tail((y0 + 1.0) / sg) - (std::isinf(y1) ? 0.0 : gauss_tail((y1 + 1.0) / sg));
+    const double w = a + b;
+    out.push_back(Cls{w, w > 0.0 ? b / w : 0.0});
+    y0 = y1;
+  }
+  return out;
+}
+
+struct Walk {
+  int n;
+  size_t M;
+  double *pe;
+  std::vector<Cls> buf;     // children of every depth: (n + 1) * M
+  std::vector<Cls> prod;
+  Merger mg;
+  Walk(int n_, size_t M_, double *pe_, size_t cap)
+      : n(n_), M(M_), pe(pe_), buf((size_t)(n_ + 1) * M_), prod(cap) {}
+  // the subtree below the channel c (L classes) at depth d, leaf index base j
+  void down(const Cls *c, size_t L, int d, uint64_t j) {
+    if (d == n) {
+      double e = 0.0;
+      for (size_t k = 0; k < L; ++k) e += c[k].w * c[k].z;
+      pe[j] = e;
+      return;
+    }
+    Cls *ch = buf.data() + (size_t)(d + 1) * M;
+    for (int side = 0; side < 2; ++side) {      // minus child (index bit 0), then plus
+      size_t m = combine(c, L, side == 1, prod.data());
+      m = mg.run(prod.data(), m, M);
+      std::copy(prod.begin(), prod.begin() + m, ch);
+      down(ch, m, d + 1, 2 * j + side);
+    }
+  }
+};
 
 }  // namespace
 
 int tv_bit_channel_pe(uint32_t log2n, polar_channel ch, double param, int mu,
                       std::vector<double> &pe) {
-  const int n = (int)log2n, M = mu / 2, M0 = 4 * M;
-  const int cap = std::max(2 * M * (M + 1), M0);
+  const int n = (int)log2n;
+  const size_t M = (size_t)mu / 2, M0 = 4 * M;
+  const size_t cap = std::max(M * (M + 1), M0) + 8;
   try {
     pe.assign(size_t(1) << n, 0.0);
   } catch (...) {
     return POLAR_ENOMEM;
   }
-  TvScratch sc0(cap);
-  int L0 = tv_start(ch, param, M0, sc0.prod.data());
-  L0 = tv_reduce(sc0.prod.data(), L0, M, sc0);
-  // breadth first down to d0 levels, then one depth-first walk per root
-  const int d0 = std::min(n, 6);
-  std::vector<TvPair> lv((size_t(1) << d0) * M);
-  std::vector<int> cnt(size_t(1) << d0);
-  std::copy(sc0.prod.begin(), sc0.prod.begin() + L0, lv.begin());
-  cnt[0] = L0;
-  for (int s = 0; s < d0; ++s) {
-    std::vector<TvPair> nx((size_t(2) << s) * M);
-    std::vector<int> nc(size_t(2) << s);
-    for (uint64_t j = 0; j < (uint64_t(1) << s); ++j)
+  std::vector<Cls> root = start_classes(ch, param, M0);
+  Merger mg0;
+  root.resize(cap);
+  const size_t L0 = mg0.run(root.data(), M0 == 0 || ch == POLAR_BSC ? 1 : M0, M);
+  // Expand the first levels breadth first (one list of channels per level),
+  // then walk each of those subtrees depth first on its own thread.
+  const int top = std::min(n, 6);
+  std::vector<std::vector<Cls>> level{std::vector<Cls>(root.begin(), root.begin() + L0)};
+  std::vector<Cls> prod(cap);
+  for (int d = 0; d < top; ++d) {
+    std::vector<std::vector<Cls>> nx;
+    nx.reserve(level.size() * 2);
+    for (const auto &c : level)
       for (int side = 0; side < 2; ++side) {
-        int c = tv_child(lv.data() + j * M, cnt[j], side == 1, sc0.prod.data());
-        c = tv_reduce(sc0.prod.data(), c, M, sc0);
-        std::copy(sc0.prod.begin(), sc0.prod.begin() + c, nx.begin() + (2 * j + side) * M);
-        nc[2 * j + side] = c;
+        size_t m = combine(c.data(), c.size(), side == 1, prod.data());
+        m = mg0.run(prod.data(), m, M);
+        nx.emplace_back(prod.begin(), prod.begin() + m);
       }
-    std::copy(nx.begin(), nx.end(), lv.begin());
-    std::copy(nc.begin(), nc.end(), cnt.begin());
+    level.swap(nx);
   }
-  const TvTree T{n, M, pe.data()};
-  const uint64_t roots = uint64_t(1) << d0;
-  std::atomic<uint64_t> next{0};
+  std::atomic<size_t> next{0};
   auto worker = [&] {
-    TvScratch sc(cap);
-    std::vector<TvPair> stack((size_t)(n + 1) * M);
+    Walk wk(n, M, pe.data(), cap);
     for (;;) {
-      const uint64_t r = next.fetch_add(1);
-      if (r >= roots) break;
-      tv_walk(T, lv.data() + r * M, cnt[r], d0, r, stack, sc);
+      const size_t r = next.fetch_add(1);
+      if (r >= level.size()) break;
+      wk.down(level[r].data(), level[r].size(), top, r);
     }
   };
   const unsigned nt = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
@@ -421,7 +453,7 @@ int tv_bit_channel_pe(uint32_t log2n, polar_channel ch, double param, int mu,
     worker();
   } else {
     std::vector<std::thread> th;
-    for (unsigned w = 0; w < nt; ++w) th.emplace_back(worker);
+    for (unsigned t = 0; t < nt; ++t) th.emplace_back(worker);
     for (auto &x : th) x.join();
   }
   return POLAR_OK;
