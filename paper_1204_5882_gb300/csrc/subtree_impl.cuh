@@ -850,25 +850,32 @@ __device__ __forceinline__ void subtree_body(const StParams &p, bool in_is_llr, 
       for (uint32_t i = tid; i < T; i += nth) Lt[i] = rnd<Tin>(src[i] * w.sc);
     }
   } else {
-    // Tin-typed level t (16-byte chunks of 4, 8 or 16 values), widened to float
+    // Tin-typed level t widened to float: a thread loads four values at a time
+    // (8 bytes of half, 4 of int8; eight loads in flight, past L1 since a node
+    // CTA writes level t with st.cg) and stores them as one float4, so a warp's
+    // shared-memory stores are consecutive 16-byte words (no bank conflicts).
     const Tin *src = reinterpret_cast<const Tin *>(p.in) + fr * p.in_stride;
-    constexpr uint32_t PER = 16 / sizeof(Tin);
-    const uint32_t n16 = T / PER;                            // T >= 32 here
-    const uint4 *s16 = reinterpret_cast<const uint4 *>(src);
-    for (uint32_t b = 0; b < n16; b += nth * 8) {
-      uint4 q[8];
+    using Q = typename std::conditional<
+        sizeof(Tin) == 2, uint2,
+        typename std::conditional<sizeof(Tin) == 1, uint32_t, uint4>::type>::type;
+    constexpr uint32_t PER = sizeof(Q) / sizeof(Tin);        // 4
+    const uint32_t nq = T / PER;                             // T >= 32 here
+    const Q *sq = reinterpret_cast<const Q *>(src);
+    for (uint32_t b = 0; b < nq; b += nth * 8) {
+      Q q[8];
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
         const uint32_t i = b + nth * r + tid;
-        if (i < n16) q[r] = __ldcg(s16 + i);       // past L1: a node CTA writes level t with st.cg
+        if (i < nq) q[r] = __ldcg(sq + i);
       }
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
         const uint32_t i = b + nth * r + tid;
-        if (i < n16) {
+        if (i < nq) {
           const Tin *e = reinterpret_cast<const Tin *>(&q[r]);
-#pragma unroll
-          for (uint32_t c = 0; c < PER; ++c) Lt[PER * i + c] = Store<Tin>::ld(e + c);
+          *reinterpret_cast<float4 *>(Lt + PER * i) =
+              make_float4(Store<Tin>::ld(e), Store<Tin>::ld(e + 1), Store<Tin>::ld(e + 2),
+                          Store<Tin>::ld(e + 3));
         }
       }
     }
