@@ -367,6 +367,25 @@ def profile_pass(P, stream, step, flush):
     return prof, prof_mode
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# dominant kernel, each from one ncu capture of that kernel in that schedule
+# (profiles/k_node_bsc_p03_n20.md); keyed by workload, frames, t, node size
+# (log2), f kind, storage and kernel.  Any other schedule reports null.
+NCU_TRAFFIC = {
+    ("bsc_p03_n20", 64, 14, 15, "minsum", "fp32", "node"): 8885504.0,
+    ("bsc_p03_n20", 64, 14, 15, "exact", "fp32", "node"): 8922368.0,
+}
+
+
+def attach_traffic(roof, wname, F, t, split, fkind, prec):
+    if not roof:
+        return
+    tr = NCU_TRAFFIC.get((wname, F, t, split, fkind, prec, roof["kernel"]))
+    if tr is not None:
+        roof["traffic"] = tr
+        roof["traffic_source"] = "ncu capture of this kernel and schedule (one launch)"
+
+
 def leg_rooflines(prof, F, t, timing, sm_count, clock_ghz, split=0):
     """Roofline of the sequential decoder -- subtree launches (2^t leaves per
     frame) and node launches (2^s leaves per frame, their levels s..t+1 run
@@ -422,7 +441,7 @@ def schedule_of(tuned, P=None):
 
 
 def decode_leg(P, dev, stream, fs, F, N, llr, fv, xd, fkind, prec, flush, steps=5, warmup=3,
-               y=None, channel=None, param=None, tune=True):
+               y=None, channel=None, param=None, tune=True, wname=None):
     """Time `steps` steps of one decode configuration on resident inputs
     (the LLR map included when y is given), same rules as the headline:
     warm-up, L2 flushed between steps, CUDA events on the launching stream;
@@ -461,6 +480,7 @@ def decode_leg(P, dev, stream, fs, F, N, llr, fv, xd, fkind, prec, flush, steps=
     props = torch.cuda.get_device_properties(dev)
     sub, streamed = leg_rooflines(prof, F, t, mode, props.multi_processor_count, 2.07,
                                   sched["node_log2"])
+    attach_traffic(sub, wname, F, t, sched["node_log2"], fkind, prec)
     return {"value": F * N / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms,
             "steps": steps, "warmup": warmup, "frames": F, "N": N, "fkind": fkind,
             "storage": prec, "fer": fer,
@@ -705,7 +725,8 @@ def run_ours(args):
         tune = not args.no_autotune and args.subtree_log2 is None
         # the paper's update (exact f) and FP16 storage on the same frames
         legs["exact_n20"] = decode_leg(P, dev, stream, fs, F, N, llr, fv, xd, "exact", "fp32",
-                                       flush, y=yd, channel=w.channel, param=w.param, tune=tune)
+                                       flush, y=yd, channel=w.channel, param=w.param, tune=tune,
+                                       wname=w.name)
         legs["fp16_n20"] = decode_leg(P, dev, stream, fs, F, N, llr, fv, xd, "minsum", "fp16",
                                       flush, y=yd, channel=w.channel, param=w.param, tune=tune)
         # the same channel and length with Sec. 3's frozen set (degraded-channel
@@ -748,12 +769,7 @@ def run_ours(args):
     clock_ghz = (ck.get("sm_max_mhz") or 2070.0) / 1e3
     roof, roof_streamed = leg_rooflines(prof, F, t, prof_mode, sm_count, clock_ghz,
                                         sched["node_log2"])
-    if (roof and w.name == "bsc_p03_n20" and F == 64 and t == 14 and sched["node_log2"] == 0
-            and args.fkind == "minsum" and args.prec == "fp32"):
-        # DRAM bytes per k_subtree launch of this schedule from one ncu capture
-        # (dram__bytes_read.sum + dram__bytes_write.sum; profiles/k_subtree_bsc_p03_n20.md)
-        roof["traffic"] = 4467968.0
-        roof["traffic_source"] = "ncu capture of this kernel and schedule (one launch)"
+    attach_traffic(roof, w.name, F, t, sched["node_log2"], args.fkind, args.prec)
     kernel_share = {k: {"ms": prof[k][0], "launches": prof[k][1]} for k in prof}
 
     cpu = None
