@@ -361,8 +361,10 @@ int polar_sc_decode_persistent(int nframes, const polar_frame_desc *frames,
  * unfused streamed steps, and (float32) with or without the subtree kernel
  * taking its parent's step; then, at the best t, node units of 2^s leaves
  * for s = t+1 .. t+4 (see "split_log2") with fused and unfused steps above
- * them -- and keeps the fastest for the batch shape (device, log2 N,
- * nframes, fkind, prec).  While the "autotune" option is 1 (default), later
+ * them -- then times every schedule within 4 % of the fastest again over
+ * eight decodes, and keeps the fastest of that round for the batch shape
+ * (device, log2 N, nframes, fkind, prec).  While the "autotune" option is 1
+ * (default), later
  * decodes of that shape use it.  Synchronous on `stream`; the batch's
  * outputs are overwritten with valid decodes.  *best_fuse receives the
  * schedule flags (bit 0: fused streamed steps, bit 1: the subtree takes its

@@ -29,7 +29,7 @@ namespace polar {
 
 namespace {
 
-constexpr uint32_t NT = 128;   // threads of a node CTA (the subtree decoder's four warps)
+constexpr uint32_t NT = 32 * kScWarps;   // threads of a node CTA (the subtree decoder's warps)
 
 struct NodeParams {
   const void *lv;           // level t of the workspace; level k at F (2^k - 2^t) values
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(NT, 1) k_node(NodeParams p) {
       if (k == t) {
         sp.o = o;
         sp.cls = p.cls ? p.cls + (o >> t) * 2 * class_words(t) : nullptr;
-        subtree_body<4, S, FK, true, UH>(sp, false, fr, smraw);
+        subtree_body<kScWarps, S, FK, true, UH>(sp, false, fr, smraw);
         break;
       }
       if (node_class(p, k - 1, o) != NODE_RATE0)
