@@ -111,8 +111,19 @@ def test_reveal_matches_oracle(P):
 
 
 # ------------------------------------------------------------------ min-sum bit-exact
+# 32-leaf frozen patterns (bit j = leaf j frozen): the five that the decoder
+# handles by compile-time decoders (repetition, 0x177F7FFF, 0x0117177F,
+# 0x00010117, single parity), rate 0 and rate 1, and three neighbours that
+# take the generic recursion.
+PATTERN_BLOCKS = (0x7FFFFFFF, 0x177F7FFF, 0x0117177F, 0x00010117, 0x00000001,
+                  0xFFFFFFFF, 0x00000000, 0x00000117, 0x0017177F, 0x077F7FFF)
+
+
 def random_code(rng, n, kind):
     N = 1 << n
+    if kind == "patterns":      # 32-leaf blocks drawn from PATTERN_BLOCKS
+        words = rng.choice(np.array(PATTERN_BLOCKS, dtype=np.uint32), max(1, N // 32))
+        return S.unpack_bits(words, N).astype(np.uint8)
     if kind == "random":
         fz = (rng.random(N) < 0.5).astype(np.uint8)
     elif kind == "all_frozen":
@@ -149,6 +160,17 @@ def test_minsum_bitexact_small(P, n, kind, t):
     P.polar_config_set("subtree_log2", t)
     check_minsum(P, n, kind, F=3, seed=1000 * n + t, llr_kind="gauss")
     check_minsum(P, n, kind, F=2, seed=1000 * n + t + 7, llr_kind="bsc")
+
+
+@pytest.mark.parametrize("t", [5, 9, 13])
+def test_minsum_frozen_pattern_decoders(P, t):
+    """Codes built from the 32-leaf patterns with compile-time decoders, with
+    Gaussian LLRs and with BSC-like +-c LLRs (exact zeros in g, which the
+    rate-1 children inside those patterns must handle): x_hat and u_hat
+    bit-exact against the oracle."""
+    P.polar_config_set("subtree_log2", t)
+    check_minsum(P, 14, "patterns", F=3, seed=4100 + t, llr_kind="gauss")
+    check_minsum(P, 14, "patterns", F=3, seed=4200 + t, llr_kind="bsc")
 
 
 @pytest.mark.parametrize("mode", ["no_shortcuts", "no_graphs", "plain", "no_fuse", "no_pdl",
@@ -339,7 +361,7 @@ def test_subtree_taking_its_parent_step_changes_no_bit(P, fkind):
         P.polar_config_set("autotune", 1)
 
 
-@pytest.mark.parametrize("kind", ["polar", "random", "all_info"])
+@pytest.mark.parametrize("kind", ["polar", "random", "all_info", "patterns"])
 def test_exact_f_same_bits_on_every_path(P, kind):
     """Every decoder path forms the same exact-f float32 values: the plain
     decoder (lane-parallel through shared memory down to single leaves), the
