@@ -202,6 +202,30 @@ __device__ __forceinline__ float load_in(const Tin *p, float sc) {
   return Store<Tin>::ld(p);
 }
 
+// Reduced storage: a thread moves 16 bytes of output per step (8 FP16 or 16
+// INT8 values) and the matching 16 or 32..64 bytes of each input operand,
+// with the per-value conversions, rounding and saturation of load_in / Store.
+template <typename Tin, typename Tout>
+struct Vec16 {
+  static constexpr int N = 16 / sizeof(Tout);                    // values per step
+  static constexpr int NIN = N * (int)sizeof(Tin) / 16;          // 16-byte loads per operand
+  static __device__ __forceinline__ void load(const Tin *p, float (&v)[N], float sc) {
+    uint4 q[NIN];
+#pragma unroll
+    for (int k = 0; k < NIN; ++k) q[k] = reinterpret_cast<const uint4 *>(p)[k];
+    const Tin *e = reinterpret_cast<const Tin *>(q);
+#pragma unroll
+    for (int c = 0; c < N; ++c) v[c] = load_in<Tin, Tout>(e + c, sc);
+  }
+  static __device__ __forceinline__ void store(Tout *p, const float (&v)[N]) {
+    uint4 q;
+    Tout *e = reinterpret_cast<Tout *>(&q);
+#pragma unroll
+    for (int c = 0; c < N; ++c) Store<Tout>::st(e + c, v[c]);
+    *reinterpret_cast<uint4 *>(p) = q;
+  }
+};
+
 template <typename Tin, typename Tout, int FK>
 __global__ void k_stream_f(const Tin *__restrict__ in, size_t in_stride, Tout *__restrict__ out,
                            size_t out_stride, uint64_t h, const float *__restrict__ scale) {
@@ -210,8 +234,9 @@ __global__ void k_stream_f(const Tin *__restrict__ in, size_t in_stride, Tout *_
   const Tin *b = a + h;
   Tout *o = out + blockIdx.y * out_stride;
   const float sc = scale ? scale[blockIdx.y] : 1.0f;
-  const uint64_t h4 = h >> 2;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < h4;
+  using V = Vec16<Tin, Tout>;
+  const uint64_t hv = h / V::N;                   // h is a power of two >= 32
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < hv;
        i += (uint64_t)gridDim.x * blockDim.x) {
     if constexpr (sizeof(Tin) == 4 && sizeof(Tout) == 4) {
       float4 x = reinterpret_cast<const float4 *>(a)[i];
@@ -223,12 +248,12 @@ __global__ void k_stream_f(const Tin *__restrict__ in, size_t in_stride, Tout *_
       z.w = f_op<FK>(x.w, y.w);
       reinterpret_cast<float4 *>(o)[i] = z;
     } else {
+      float x[V::N], y[V::N];
+      V::load(a + i * V::N, x, sc);
+      V::load(b + i * V::N, y, sc);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        uint64_t j = 4 * i + c;
-        Store<Tout>::st(o + j, f_st<Tout, FK>(load_in<Tin, Tout>(a + j, sc),
-                                              load_in<Tin, Tout>(b + j, sc), sc));
-      }
+      for (int c = 0; c < V::N; ++c) x[c] = f_st<Tout, FK>(x[c], y[c], sc);
+      V::store(o + i * V::N, x);
     }
   }
 }
@@ -243,10 +268,12 @@ __global__ void k_stream_g(const Tin *__restrict__ in, size_t in_stride, Tout *_
   Tout *o = out + blockIdx.y * out_stride;
   const uint32_t *beta = xhat + blockIdx.y * x_stride + (o_bits >> 5);
   const float sc = scale ? scale[blockIdx.y] : 1.0f;
-  const uint64_t h4 = h >> 2;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < h4;
+  using V = Vec16<Tin, Tout>;
+  const uint64_t hv = h / V::N;                   // h is a power of two >= 32
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < hv;
        i += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t bits = (beta[i >> 3] >> ((i & 7) * 4)) & 0xFu;
+    const uint64_t e0 = i * V::N;                 // first value of this step
+    const uint32_t bits = (beta[e0 >> 5] >> (e0 & 31)) & ((1u << V::N) - 1u);
     if constexpr (sizeof(Tin) == 4 && sizeof(Tout) == 4) {
       float4 x = reinterpret_cast<const float4 *>(a)[i];
       float4 y = reinterpret_cast<const float4 *>(b)[i];
@@ -257,19 +284,19 @@ __global__ void k_stream_g(const Tin *__restrict__ in, size_t in_stride, Tout *_
       z.w = g_op(x.w, y.w, bits & 8u);
       reinterpret_cast<float4 *>(o)[i] = z;
     } else {
+      float x[V::N], y[V::N];
+      V::load(a + e0, x, sc);
+      V::load(b + e0, y, sc);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        uint64_t j = 4 * i + c;
-        Store<Tout>::st(o + j, g_op(load_in<Tin, Tout>(a + j, sc), load_in<Tin, Tout>(b + j, sc),
-                                    (bits >> c) & 1u));
-      }
+      for (int c = 0; c < V::N; ++c) x[c] = g_op(x[c], y[c], (bits >> c) & 1u);
+      V::store(o + e0, x);
     }
   }
 }
 
-static dim3 stream_grid(uint64_t h, int nframes) {
-  uint64_t h4 = h >> 2;
-  uint64_t want = (h4 + 255) / 256;
+// units = thread steps per frame (h / Vec16<., T>::N values each).
+static dim3 stream_grid(uint64_t units, int nframes) {
+  uint64_t want = (units + 255) / 256;
   uint64_t cap = (uint64_t)(152 * 8 + nframes - 1) / nframes;   // ~8 CTAs/SM overall
   if (cap < 1) cap = 1;
   if (want > cap) want = cap;
@@ -281,7 +308,7 @@ template <typename T>
 static cudaError_t stream_f_t(int fkind, const void *in, size_t in_stride, bool in_is_llr,
                               void *out, size_t out_stride, uint64_t h, int nframes,
                               const float *scale, cudaStream_t s) {
-  dim3 g = stream_grid(h, nframes);
+  dim3 g = stream_grid(h / (16 / sizeof(T)), nframes);
   cudaError_t e;
   if (in_is_llr) {
     e = fkind == 0 ? launch_k(k_stream_f<float, T, 0>, g, 256, 0, s, (const float *)in,
@@ -302,7 +329,7 @@ static cudaError_t stream_g_t(const void *in, size_t in_stride, bool in_is_llr, 
                               size_t out_stride, uint64_t h, const uint32_t *xhat,
                               size_t xs, uint64_t o, int nframes, const float *scale,
                               cudaStream_t s) {
-  dim3 g = stream_grid(h, nframes);
+  dim3 g = stream_grid(h / (16 / sizeof(T)), nframes);
   cudaError_t e =
       in_is_llr ? launch_k(k_stream_g<float, T>, g, 256, 0, s, (const float *)in, in_stride,
                            (T *)out, out_stride, h, xhat, xs, o, scale)
