@@ -52,3 +52,31 @@ def test_served_code_grid():
             assert abs(round(sigma, 2) - sigma) < 1e-9
         seen.add((log2n, ch))
     assert len(seen) == 8
+
+
+def test_rooflines_and_captured_traffic():
+    """The sequential decoder's roofline (f / g evaluations per launch over
+    the event time, against the FP32-lane peak; ns per leaf per frame), the
+    streamed stages' algorithmic bytes over their event time against the HBM
+    peak, and the DRAM bytes of an ncu capture attached only to the schedule
+    it was taken on."""
+    F, t, s = 64, 14, 15
+    prof = {"subtree": (0.0, 0, 0.0), "node": (8.0, 32, 0.0), "chain": (0.0, 0, 0.0),
+            "stream_f": (0.40, 31, 31 * 50e6), "stream_g": (0.45, 31, 31 * 55e6)}
+    sub, st = bench.leg_rooflines(prof, F, t, "events", 152, 2.07, s)
+    ops = 32 * F * s * 2 ** s
+    assert sub["kernel"] == "node" and sub["launches"] == 32
+    assert sub["achieved"] == pytest.approx(ops / 8.0e-3 / 1e12)
+    assert sub["peak"] == pytest.approx(152 * 128 * 2.07 / 1e3)
+    assert sub["frac"] == pytest.approx(sub["achieved"] / sub["peak"])
+    assert sub["ns_per_leaf_per_frame"] == pytest.approx(8.0e6 / (32 * 2 ** s))
+    hbm = (bench.measured_peaks() or {}).get("hbm_gbs", 6800.0)
+    assert st["achieved"] == pytest.approx(31 * (50e6 + 55e6) / 0.85e-3 / 1e9)
+    assert st["frac"] == pytest.approx(st["achieved"] / hbm)
+    assert st["launches"] == 62 and sub["traffic"] is None
+    bench.attach_traffic(sub, "bsc_p03_n20", F, t, s, "minsum", "fp32")
+    assert sub["traffic"] == bench.NCU_TRAFFIC[("bsc_p03_n20", F, t, s, "minsum", "fp32", "node")]
+    for key in (("bsc_p03_n20", F, 13, s), ("bsc_p03_n20", F, t, 16), ("biawgn_s1_n24", 16, t, s)):
+        other, _ = bench.leg_rooflines(prof, F, t, "events", 152, 2.07, s)
+        bench.attach_traffic(other, *key, "minsum", "fp32")
+        assert other["traffic"] is None, key
